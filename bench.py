@@ -1,0 +1,379 @@
+"""Benchmark of the fused cascaded-LBM step on the lid-driven cubic cavity.
+
+One step = one time step of the three 128^3 cavities at Re = 100 with
+n = 0.5, 1.0 and 1.5 (lid U = 0.05), each a separate lattice on the same
+stream.  ``value`` is the whole-job MLUPS of the FP32-storage form (fluid
+nodes x steps / seconds / 1e6, CUDA events on the launching stream, inputs
+resident in HBM).  The FP64 and FP16-shifted forms are timed the same way and
+reported under ``forms``, each against the HBM roofline of its bytes per
+lattice update, 19 reads + 19 writes x bytes per population.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (the
+reference arm): the same workload and metric, one oracle step per step.
+
+Multi-GPU (torchrun, one rank per GPU): every rank runs its own replica of
+the workload (weak scaling, no collective in the data path); a barrier
+brackets the timed region and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline, FP64 vs FP32/FP16-store; served solves/s, p50/p99"
+BYTES_PER_POP = {"f64": 8, "f32": 4, "f16s": 2}
+L_BENCH = 128
+RE_BENCH = 100.0
+NS_BENCH = (0.5, 1.0, 1.5)
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.path is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_note(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the
+    current kernel sources (else null)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    csrc = os.path.join(ROOT, "paper_1908_05396_gb300", "csrc")
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    digest = h.hexdigest()[:16]
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
+            return float(parts[2])
+    return None
+
+
+def _oracle_lattices(nz: int | None = None):
+    import oracle
+    from paper_1908_05396_gb300 import workloads as wl
+    oracle.build()
+    out = []
+    for n in NS_BENCH:
+        prob = wl.cavity(L_BENCH, RE_BENCH, n)
+        p = oracle.Params(nx=prob.nx, ny=prob.ny, nz=nz or prob.nz, face=prob.face, K=prob.K,
+                          n=prob.n, U=prob.U_lid)
+        out.append([p, oracle.rest_state(p), p.N])
+    return oracle, out
+
+
+def _cpu_baseline(budget_s: float = 12.0):
+    """The FP64 oracle on the host cores, a bounded sample of the same workload:
+    whole oracle steps of the three 128^3 cavities until the budget is spent."""
+    oracle, lats = _oracle_lattices()
+    cores = int(os.environ.get("OMP_NUM_THREADS", "0")) or (os.cpu_count() or 1)
+    nodes, steps = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        for lt in lats:
+            lt[1] = oracle.run(lt[0], lt[1], 1)
+            nodes += lt[2]
+        steps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": nodes / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} oracle step(s) of the three 128^3 Re=100 cavities "
+                      f"(n=0.5,1,1.5), FP64, OpenMP over z-planes, {dt:.1f} s"}
+
+
+REF_SLAB = 8   # z-planes of each cavity per reference step (same per-node work)
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    oracle, lats = _oracle_lattices(nz=REF_SLAB)
+    cores = int(os.environ.get("OMP_NUM_THREADS", "0")) or (os.cpu_count() or 1)
+    for _ in range(args.warmup):
+        for lt in lats:
+            lt[1] = oracle.run(lt[0], lt[1], 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for lt in lats:
+            lt[1] = oracle.run(lt[0], lt[1], 1)
+    dt = time.perf_counter() - t0
+    nodes = sum(lt[2] for lt in lats) * args.steps
+    v = nodes / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "lid-driven cubic cavity 128^3 x3 (Re=100, n=0.5/1.0/1.5, U=0.05)",
+                   "storage": "f64", "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} oracle steps of a 128x128x{REF_SLAB} slab of "
+                                   "each of the three cavities (walls on all faces, lid +y)"},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def _time_form(clbm, torch, dtype, steps, warmup, stream):
+    """MLUPS of one storage form over the three cavities on one stream."""
+    from paper_1908_05396_gb300 import workloads as wl
+    lats = [clbm.Lattice(**wl.cavity(L_BENCH, RE_BENCH, n).kwargs(), dtype=dtype,
+                         stream=stream.cuda_stream) for n in NS_BENCH]
+    N = lats[0].N
+    for _ in range(warmup):
+        for lt in lats:
+            lt.step(1)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        for lt in lats:
+            lt.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    for lt in lats:
+        lt.close()
+    launches = steps * len(lats)
+    return ms, N, launches
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1908_05396_gb300 import build, workloads as wl
+    build.build()
+    from paper_1908_05396_gb300 import clbm
+    clbm.lib()
+    peak, peak_kind = _peaks()
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- headline: FP32 storage ---------------------------------------------
+    head = "f32"
+    # untimed warm-up of every lattice (also builds nothing new)
+    barrier()
+    with Clocks(local) as clk:
+        barrier()
+        ms, N, launches = _time_form(clbm, torch, head, args.steps, args.warmup, stream)
+        barrier()
+    clocks = clk.summary()
+    ms_t = torch.tensor([ms], device="cuda")
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    nodes = N * len(NS_BENCH) * args.steps
+    value = nodes * ws / (ms_max * 1e-3) / 1e6
+    per_launch_s = ms * 1e-3 / launches
+    bpn = 38 * BYTES_PER_POP[head]
+    achieved = bpn * N / per_launch_s / 1e9
+    kern = "step_kernel<float,float,false,false>"
+    traffic = _traffic_note(kern)
+
+    # ---- the other forms ------------------------------------------------------
+    forms = {}
+    form_steps = {"f64": max(3, args.steps // 40), "f16s": args.steps}
+    for dt in ("f64", "f16s"):
+        if args.forms and dt not in args.forms:
+            continue
+        barrier()
+        ms_f, N_f, launches_f = _time_form(clbm, torch, dt, form_steps[dt], args.warmup, stream)
+        mlups = N_f * len(NS_BENCH) * form_steps[dt] / (ms_f * 1e-3) / 1e6
+        gbs = 38 * BYTES_PER_POP[dt] * N_f * launches_f / (ms_f * 1e-3) / 1e9
+        forms[dt] = {"MLUPS": mlups, "GB/s": gbs, "frac_of_hbm": gbs / peak,
+                     "steps": form_steps[dt], "bytes_per_update": 38 * BYTES_PER_POP[dt]}
+    forms[head] = {"MLUPS": value / ws, "GB/s": achieved, "frac_of_hbm": achieved / peak,
+                   "steps": args.steps, "bytes_per_update": bpn}
+
+    # ---- end to end through the C ABI with host buffers ------------------------
+    import numpy as np
+    e2e_steps = args.steps
+    prob = wl.cavity(L_BENCH, RE_BENCH, NS_BENCH[0])
+    with clbm.Lattice(**prob.kwargs(), dtype=head) as lat:
+        f0 = lat.get_state()          # host copy of the initial state
+    barrier()
+    t0 = time.perf_counter()
+    with clbm.Lattice(**prob.kwargs(), dtype=head) as lat:
+        lat.set_state(f0)             # H2D of the inputs
+        lat.step(e2e_steps)
+        rho, u, gd = lat.fields()     # D2H of the result
+    t1 = time.perf_counter()
+    e2e_val = prob.N * e2e_steps / (t1 - t0) / 1e6 * ws
+    h2d = f0.nbytes / e2e_steps
+    d2h = (rho.nbytes + u.nbytes + gd.nbytes) / e2e_steps
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = _cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "lid-driven cubic cavity 128^3 x3 (Re=100, n=0.5/1.0/1.5, "
+                                   "U=0.05), one lattice per n, FP32 storage",
+                       "storage": head, "nodes_per_step": N * len(NS_BENCH),
+                       "l2": "inputs larger than L2: 159 MB read + 159 MB written per lattice step"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind, "kernel": kern,
+                         "algorithmic_bytes_per_launch": bpn * N},
+            "forms": forms,
+            "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "what": f"create + set_state from host + {e2e_steps} steps + fields to host, "
+                            "one 128^3 n=0.5 cavity, FP32 storage, wall clock"},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_profile(args):
+    """The profiling case: FP32 steps of one 128^3 cavity (n = 0.5)."""
+    import torch
+    from paper_1908_05396_gb300 import build, workloads as wl
+    build.build()
+    from paper_1908_05396_gb300 import clbm
+    stream = torch.cuda.Stream()
+    lat = clbm.Lattice(**wl.cavity(L_BENCH, RE_BENCH, 0.5).kwargs(), dtype="f32",
+                       stream=stream.cuda_stream)
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps({"case": "f32 128^3 cavity n=0.5", "steps": args.steps,
+                      "us_per_step": ms * 1e3 / args.steps,
+                      "MLUPS": lat.N * args.steps / (ms * 1e-3) / 1e6}))
+    lat.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--forms", nargs="*", default=None)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="time only the FP32 step of the n=0.5 cavity (profiling case)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.profile:
+        return run_profile(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,159 @@
+/*
+ * clbm.h -- C ABI of the GB300 cascaded D3Q19 lattice Boltzmann library for
+ * power-law fluids.
+ *
+ * The method is the 3D cascaded (central-moment, multiple-relaxation-time)
+ * LBM of Adam, Hajabdollahi & Premnath, "Cascaded lattice Boltzmann modeling
+ * and simulations of three-dimensional non-Newtonian fluid flows":
+ *   - D3Q19 velocity set, Eq. velocityd3qq19 (direction order as the paper's
+ *     component vectors |e_x>, |e_y>, |e_z> of Sec. 3);
+ *   - cascaded collision f~ = f + K g^, Eqs. cascadecollision1 and
+ *     cascadedcollision1, with g^_4..g^_18 from Eqs. collisionkernelg4..g18;
+ *   - second-order rates omega_4..8 set at every node from the shear rate,
+ *     Eq. localvarationsrelaxationtimes with the power law of Eq. 6 and the
+ *     strain rate of Eq. strainratetensor; omega_9..18 = 1 (Sec. 3.1);
+ *   - streaming, Eq. cascadedstreaming1, with halfway bounce-back walls, a
+ *     moving lid with a momentum correction and periodic faces (Sec. 4).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status: CLBM_OK (0) or a negative
+ *     CLBM_ERR_* code.  No C++ exception crosses this interface.  The text of
+ *     the last error of a handle is returned by clbm_last_error().
+ *   - Field arrays use the unpadded layout [z][y][x], x fastest, N = nx*ny*nz
+ *     entries.  Vector fields are 3 consecutive such arrays (x, then y, then z
+ *     component).  Population arrays are 19 consecutive such arrays, in the
+ *     direction order above, holding plain (unshifted) FP64 values f_alpha.
+ *   - The caller owns every host and device buffer it passes in.  The library
+ *     owns the device memory of a handle (populations, work buffers) and frees
+ *     it in clbm_destroy().
+ *   - Work is queued on the handle's CUDA stream.  Calls that return data to
+ *     the host synchronise that stream; clbm_step() does not.
+ *   - A handle is not thread-safe: use one handle per thread, or serialise.
+ *   - One GPU: the handle lives on the device that is current when
+ *     clbm_create() is called; the library makes that device current again in
+ *     every call on the handle.
+ */
+#ifndef CLBM_H
+#define CLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define CLBM_OK 0
+#define CLBM_ERR_ARG -1         /* invalid argument or handle */
+#define CLBM_ERR_OOM -2         /* device memory allocation failed */
+#define CLBM_ERR_CUDA -3        /* CUDA runtime error */
+#define CLBM_ERR_DIVERGED -4    /* NaN/Inf or density outside [0.5, 2] seen */
+#define CLBM_ERR_TIMEOUT -5     /* a bounded device wait gave up */
+#define CLBM_ERR_UNSUPPORTED -6 /* valid request this build does not support */
+
+/* Storage precision of the populations.
+ *   CLBM_F64  : f - w rho0 stored in FP64, collision in FP64.
+ *   CLBM_F32  : f - w rho0 stored in FP32, collision in FP32.
+ *   CLBM_F16S : (f - w rho0) * 1024 stored in FP16 (round to nearest even),
+ *               collision in FP32.
+ * Residual and mass reductions accumulate in FP64 for every form. */
+typedef enum { CLBM_F64 = 0, CLBM_F32 = 1, CLBM_F16S = 2 } clbm_dtype;
+
+/* Face kinds, for faces ordered (-x, +x, -y, +y, -z, +z).
+ *   CLBM_PERIODIC : both faces of the pair must be periodic.
+ *   CLBM_WALL     : halfway bounce-back, no slip (Sec. 4.1, 4.2).
+ *   CLBM_LID      : halfway bounce-back plus the momentum correction
+ *                   6 w_alpha rho0 (e_alpha . U_lid) of a wall moving with
+ *                   velocity U_lid (Sec. 4.3).  U_lid must be tangential to
+ *                   every LID face.  Where a link crosses a lid and another
+ *                   wall (edges, corners), the lid rule applies. */
+typedef enum { CLBM_PERIODIC = 0, CLBM_WALL = 1, CLBM_LID = 2 } clbm_bc;
+
+typedef struct {
+  int nx, ny, nz;      /* lattice nodes per axis, each >= 1 */
+  int face[6];         /* clbm_bc of faces -x, +x, -y, +y, -z, +z */
+  double rho0;         /* reference density (rest state, lid); 0 -> 1 */
+  double nu_min;       /* kinematic-viscosity clamp; 0 -> 5e-4 */
+  double nu_max;       /* 0 -> 10 */
+  int check_interval;  /* steps between residual checks; 0 -> 100 */
+  void* stream;        /* cudaStream_t to queue on; NULL -> library-owned */
+} clbm_domain;
+
+typedef struct clbm_ctx* clbm_handle;
+
+/* Create a lattice in the rest state f = w rho0 (Sec. 3; initial state not
+ * stated by the paper).
+ *   K          consistency coefficient mu_p of Eq. 5, > 0.
+ *   n          power-law index of Eq. 5, in (0, 3].
+ *   U_lid      velocity of LID faces (3 doubles); may be NULL if no LID face;
+ *              |U_lid| must be < 0.3.
+ *   body_force force per unit volume (3 doubles), NULL -> 0; applied by a
+ *              symmetric split, half before and half after the collision.
+ *   dtype      storage precision.
+ *   out        receives the handle.
+ * Errors: CLBM_ERR_ARG (bad sizes or parameters), CLBM_ERR_OOM, CLBM_ERR_CUDA. */
+int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
+                const double body_force[3], clbm_dtype dtype,
+                clbm_handle* out);
+
+/* Queue nsteps time steps (pull-stream + collide, Eqs. cascadedstreaming1 and
+ * cascadedcollision1) on the handle's stream and return.  Every step whose
+ * global index is a multiple of check_interval also writes u and reduces the
+ * residual, the mass and a divergence flag in FP64.
+ * Returns CLBM_ERR_DIVERGED if an earlier, already completed check found a
+ * non-finite value or a density outside [0.5, 2]; the queued steps still run. */
+int clbm_step(clbm_handle h, int64_t nsteps);
+
+/* Macroscopic fields of the current state (Eqs. hydrodynamicfields1/2,
+ * shearrateexpression): rho (N), u (3N, the half-force velocity
+ * (j + F/2)/rho) and |gamma_dot| (N), computed from the streamed
+ * populations.  Host pointers; any may be NULL.  Synchronises the stream. */
+int clbm_fields(clbm_handle h, double* rho, double* u, double* gamma_dot);
+
+/* As clbm_fields, into device pointers on the handle's device. */
+int clbm_fields_device(clbm_handle h, double* rho, double* u,
+                       double* gamma_dot);
+
+/* Last steady-state residual R = ||u - u_prev|| / (check_interval ||u||)
+ * over all nodes (FP64); +Inf before the second check.  Synchronises.
+ * Returns CLBM_ERR_DIVERGED (and still writes R) if divergence was seen. */
+int clbm_residual(clbm_handle h, double* out);
+
+/* Total mass sum(rho) at the last check step (FP64).  Synchronises. */
+int clbm_mass(clbm_handle h, double* out);
+
+/* Copy the stored populations to / from the host as plain FP64 f
+ * (19 x N, layout above).  Synchronises. */
+int clbm_get_state(clbm_handle h, double* f_host);
+int clbm_set_state(clbm_handle h, const double* f_host);
+
+/* Steps run so far. */
+int clbm_steps_done(clbm_handle h, int64_t* out);
+
+/* Wait for all queued work of the handle. */
+int clbm_sync(clbm_handle h);
+
+/* Free the handle and its device memory.  NULL is accepted. */
+int clbm_destroy(clbm_handle h);
+
+/* Text of the last error on h (never NULL); h may be NULL for errors of
+ * clbm_create. */
+const char* clbm_last_error(clbm_handle h);
+
+/* Collide M independent nodes without streaming (Eqs. cascadecollision1,
+ * cascadedcollision1): f_in and f_out are host arrays of 19 x M plain FP64
+ * populations, [alpha][node].  The node states are stored in dtype first
+ * (so F16S/F32 see their storage rounding), collided with the parameters
+ * K, n, body_force, rho0, nu_min, nu_max (0 -> defaults) on the current
+ * device, and returned.  rho, u (3 x M) and gamma_dot, if not NULL, receive
+ * the per-node fields.  Synchronous. */
+int clbm_collide_nodes(clbm_dtype dtype, double K, double n,
+                       const double body_force[3], double rho0, double nu_min,
+                       double nu_max, const double* f_in, double* f_out,
+                       double* rho, double* u, double* gamma_dot, int64_t M);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,214 @@
+"""Thin ctypes binding of the C ABI in ``include/clbm.h``.
+
+Argument marshalling only: every step of the method runs inside
+``libclbm.so``.  There is no CPU fallback; if the library has not been built
+(``paper_1908_05396_gb300.build.build()``), importing the library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+F64, F32, F16S = 0, 1, 2
+PERIODIC, WALL, LID = 0, 1, 2
+DTYPES = {"f64": F64, "f32": F32, "f16s": F16S}
+
+_LOCK = threading.Lock()
+_LIB = None
+
+
+class CLBMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"clbm error {code}: {msg}")
+        self.code = code
+
+
+class Domain(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("face", ctypes.c_int * 6), ("rho0", ctypes.c_double),
+                ("nu_min", ctypes.c_double), ("nu_max", ctypes.c_double),
+                ("check_interval", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_H = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load ``libclbm.so`` (raises if it has not been built)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise ImportError(f"libclbm.so not built at {path}; run "
+                                  "paper_1908_05396_gb300.build.build() first")
+            L = ctypes.CDLL(path)
+            L.clbm_create.argtypes = [ctypes.POINTER(Domain), ctypes.c_double, ctypes.c_double,
+                                      _D, _D, ctypes.c_int, ctypes.POINTER(_H)]
+            L.clbm_step.argtypes = [_H, ctypes.c_int64]
+            L.clbm_fields.argtypes = [_H, _D, _D, _D]
+            L.clbm_fields_device.argtypes = [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+            L.clbm_residual.argtypes = [_H, _D]
+            L.clbm_mass.argtypes = [_H, _D]
+            L.clbm_get_state.argtypes = [_H, _D]
+            L.clbm_set_state.argtypes = [_H, _D]
+            L.clbm_steps_done.argtypes = [_H, ctypes.POINTER(ctypes.c_int64)]
+            L.clbm_sync.argtypes = [_H]
+            L.clbm_destroy.argtypes = [_H]
+            L.clbm_last_error.argtypes = [_H]
+            L.clbm_last_error.restype = ctypes.c_char_p
+            L.clbm_collide_nodes.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _D,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             _D, _D, _D, _D, _D, ctypes.c_int64]
+            for name in ("clbm_create", "clbm_step", "clbm_fields", "clbm_fields_device",
+                         "clbm_residual", "clbm_mass", "clbm_get_state", "clbm_set_state",
+                         "clbm_steps_done", "clbm_sync", "clbm_destroy", "clbm_collide_nodes"):
+                getattr(L, name).restype = ctypes.c_int
+            _LIB = L
+    return _LIB
+
+
+def _dp(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_D)
+
+
+def _vec3(v):
+    if v is None:
+        return None
+    return (ctypes.c_double * 3)(*[float(x) for x in v])
+
+
+def _check(rc: int, h=None):
+    if rc != OK:
+        msg = lib().clbm_last_error(h)
+        raise CLBMError(rc, msg.decode() if msg else "")
+
+
+class Lattice:
+    """One lattice on the current CUDA device (a ``clbm_handle``)."""
+
+    def __init__(self, nx, ny, nz, face=(PERIODIC,) * 6, K=0.1, n=1.0, U_lid=None,
+                 body_force=None, dtype="f64", rho0=1.0, nu_min=0.0, nu_max=0.0,
+                 check_interval=100, stream=None):
+        L = lib()
+        d = Domain()
+        d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
+        for i, f in enumerate(face):
+            d.face[i] = int(f)
+        d.rho0, d.nu_min, d.nu_max = float(rho0), float(nu_min), float(nu_max)
+        d.check_interval = int(check_interval)
+        d.stream = stream
+        self.shape = (int(nz), int(ny), int(nx))
+        self.N = int(nx) * int(ny) * int(nz)
+        self.dtype = dtype
+        self.check_interval = int(check_interval)
+        h = _H()
+        code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        _check(L.clbm_create(ctypes.byref(d), float(K), float(n), _vec3(U_lid),
+                             _vec3(body_force), code, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def step(self, nsteps: int) -> int:
+        rc = lib().clbm_step(self._h, int(nsteps))
+        if rc not in (OK, ERR_DIVERGED):
+            _check(rc, self._h)
+        return rc
+
+    def fields(self):
+        """(rho (nz,ny,nx), u (3,nz,ny,nx), gamma_dot (nz,ny,nx)) as FP64 numpy arrays."""
+        rho = np.empty(self.shape)
+        u = np.empty((3,) + self.shape)
+        gd = np.empty(self.shape)
+        _check(lib().clbm_fields(self._h, _dp(rho), _dp(u), _dp(gd)), self._h)
+        return rho, u, gd
+
+    def fields_device(self, rho=None, u=None, gamma_dot=None):
+        """Write the fields into caller-owned CUDA tensors (float64, contiguous)."""
+        def ptr(t, n):
+            if t is None:
+                return None
+            assert t.is_cuda and t.dtype.itemsize == 8 and t.is_contiguous() and t.numel() == n
+            return ctypes.c_void_p(t.data_ptr())
+        _check(lib().clbm_fields_device(self._h, ptr(rho, self.N), ptr(u, 3 * self.N),
+                                        ptr(gamma_dot, self.N)), self._h)
+
+    def residual(self) -> tuple[float, int]:
+        out = ctypes.c_double(0.0)
+        rc = lib().clbm_residual(self._h, ctypes.byref(out))
+        if rc not in (OK, ERR_DIVERGED):
+            _check(rc, self._h)
+        return out.value, rc
+
+    def mass(self) -> float:
+        out = ctypes.c_double(0.0)
+        _check(lib().clbm_mass(self._h, ctypes.byref(out)), self._h)
+        return out.value
+
+    def get_state(self) -> np.ndarray:
+        f = np.empty((19,) + self.shape)
+        _check(lib().clbm_get_state(self._h, _dp(f)), self._h)
+        return f
+
+    def set_state(self, f: np.ndarray) -> None:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (19,) + self.shape
+        _check(lib().clbm_set_state(self._h, _dp(f)), self._h)
+
+    def steps_done(self) -> int:
+        out = ctypes.c_int64(0)
+        _check(lib().clbm_steps_done(self._h, ctypes.byref(out)), self._h)
+        return out.value
+
+    def sync(self) -> None:
+        _check(lib().clbm_sync(self._h), self._h)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().clbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def collide_nodes(f: np.ndarray, K: float, n: float, dtype="f64", body_force=None, rho0=1.0,
+                  nu_min=0.0, nu_max=0.0):
+    """Collide M independent nodes on the GPU: f is (19, M) plain FP64."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    M = f.shape[1]
+    out = np.empty_like(f)
+    rho = np.empty(M)
+    u = np.empty((3, M))
+    gd = np.empty(M)
+    code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    _check(lib().clbm_collide_nodes(code, float(K), float(n), _vec3(body_force), float(rho0),
+                                    float(nu_min), float(nu_max), _dp(f), _dp(out), _dp(rho),
+                                    _dp(u), _dp(gd), M))
+    return dict(ft=out, rho=rho, u=u, gamma_dot=gd)

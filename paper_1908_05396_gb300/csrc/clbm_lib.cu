@@ -1,0 +1,437 @@
+// clbm_lib.cu -- host side of the C ABI declared in include/clbm.h.
+//
+// A handle owns two population buffers (A-B), the check-step work buffers and
+// a stream.  clbm_step() queues kernels and returns; check steps copy their
+// FP64 reduction results into pinned host memory behind an event, so the host
+// learns about divergence without stalling the stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/clbm.h"
+#include "launch.h"
+
+using namespace clbm;
+
+struct clbm_ctx {
+  int device = 0;
+  clbm_domain dom{};
+  clbm_dtype dtype = CLBM_F64;
+  Geom g{};
+  PhysParams P{};
+  size_t elem = 8;       // bytes per stored population
+  size_t rsize = 8;      // bytes per math-precision value
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;           // buffer holding the current state
+  void* uprev = nullptr;
+  double* acc = nullptr; // device: 3 doubles, then the int flag
+  int* flag = nullptr;
+  double* host = nullptr; // pinned: acc[3], flag as double
+  cudaEvent_t check_done = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t steps = 0;
+  int64_t checks = 0;    // check steps queued so far
+  bool diverged = false; // sticky once a completed check saw divergence
+  dim3 block{32, 4, 1};
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(clbm_ctx* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+int cuda_fail(clbm_ctx* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(h, e == cudaErrorMemoryAllocation ? CLBM_ERR_OOM : CLBM_ERR_CUDA, m);
+}
+
+#define CK(h, expr)                                   \
+  do {                                                \
+    cudaError_t e_ = (expr);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #expr); \
+  } while (0)
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+cudaError_t dispatch_step(clbm_ctx* h, bool check) {
+  CheckBufs cb{h->uprev, h->acc, h->flag};
+  const void* src = h->buf[h->cur];
+  void* dst = h->buf[1 - h->cur];
+  switch (h->dtype) {
+    case CLBM_F64: return launch_step_f64(src, dst, h->g, h->P, cb, check, h->block, h->stream);
+    case CLBM_F32: return launch_step_f32(src, dst, h->g, h->P, cb, check, h->block, h->stream);
+    default: return launch_step_f16(src, dst, h->g, h->P, cb, check, h->block, h->stream);
+  }
+}
+
+int set_device(clbm_ctx* h) {
+  CK(h, cudaSetDevice(h->device));
+  return CLBM_OK;
+}
+
+bool bad(const clbm_ctx* h) { return h == nullptr || h->buf[0] == nullptr; }
+
+void fill_params(PhysParams& P, double K, double n, const double* F, double rho0,
+                 double nu_min, double nu_max, clbm_dtype dtype) {
+  P.rho0 = rho0;
+  for (int a = 0; a < 3; ++a) P.F[a] = F ? F[a] : 0.0;
+  P.has_force = (P.F[0] != 0.0 || P.F[1] != 0.0 || P.F[2] != 0.0) ? 1 : 0;
+  P.K = K;
+  P.logK3 = std::log(3.0 * K);
+  P.n = n;
+  P.newtonian = (n == 1.0) ? 1 : 0;
+  P.nu_min = nu_min;
+  P.nu_max = nu_max;
+  P.ylo = std::log(3.0 * nu_min);
+  P.yhi = std::log(3.0 * nu_max);
+  P.inv_scale = dtype == CLBM_F16S ? 1.0 / F16_SCALE : 1.0;
+}
+
+int check_phys(double K, double n, double nu_min, double nu_max, std::string& why) {
+  if (!(K > 0.0) || !std::isfinite(K)) { why = "K must be finite and > 0"; return 0; }
+  if (!(n > 0.0 && n <= 3.0)) { why = "n must lie in (0, 3]"; return 0; }
+  if (!(nu_min > 0.0 && nu_max > nu_min) || !std::isfinite(nu_max)) {
+    why = "need 0 < nu_min < nu_max < inf";
+    return 0;
+  }
+  return 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
+                const double body_force[3], clbm_dtype dtype, clbm_handle* out) {
+  if (!d || !out) return fail(nullptr, CLBM_ERR_ARG, "null domain or output pointer");
+  *out = nullptr;
+  if (dtype != CLBM_F64 && dtype != CLBM_F32 && dtype != CLBM_F16S)
+    return fail(nullptr, CLBM_ERR_ARG, "unknown dtype");
+  if (d->nx < 1 || d->ny < 1 || d->nz < 1)
+    return fail(nullptr, CLBM_ERR_ARG, "lattice dimensions must be >= 1");
+  const int64_t N = int64_t(d->nx) * d->ny * d->nz;
+  if (N > (int64_t(1) << 34)) return fail(nullptr, CLBM_ERR_ARG, "lattice too large");
+  bool has_lid = false;
+  for (int f = 0; f < 6; ++f) {
+    if (d->face[f] < CLBM_PERIODIC || d->face[f] > CLBM_LID)
+      return fail(nullptr, CLBM_ERR_ARG, "unknown face kind");
+    has_lid = has_lid || d->face[f] == CLBM_LID;
+  }
+  for (int a = 0; a < 3; ++a)
+    if ((d->face[2 * a] == CLBM_PERIODIC) != (d->face[2 * a + 1] == CLBM_PERIODIC))
+      return fail(nullptr, CLBM_ERR_ARG, "a periodic face needs a periodic opposite face");
+  double U[3] = {0, 0, 0};
+  if (U_lid)
+    for (int a = 0; a < 3; ++a) U[a] = U_lid[a];
+  if (has_lid) {
+    if (!U_lid) return fail(nullptr, CLBM_ERR_ARG, "LID face without U_lid");
+    const double mag = std::sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
+    if (!(mag < 0.3)) return fail(nullptr, CLBM_ERR_ARG, "|U_lid| must be < 0.3");
+    for (int f = 0; f < 6; ++f)
+      if (d->face[f] == CLBM_LID && U[f / 2] != 0.0)
+        return fail(nullptr, CLBM_ERR_ARG, "U_lid must be tangential to every LID face");
+  }
+  const double rho0 = d->rho0 > 0.0 ? d->rho0 : 1.0;
+  const double nu_min = d->nu_min > 0.0 ? d->nu_min : 5e-4;
+  const double nu_max = d->nu_max > 0.0 ? d->nu_max : 10.0;
+  std::string why;
+  if (!check_phys(K, n, nu_min, nu_max, why)) return fail(nullptr, CLBM_ERR_ARG, why);
+  if (body_force)
+    for (int a = 0; a < 3; ++a)
+      if (!std::isfinite(body_force[a])) return fail(nullptr, CLBM_ERR_ARG, "non-finite force");
+
+  clbm_ctx* h = new (std::nothrow) clbm_ctx();
+  if (!h) return fail(nullptr, CLBM_ERR_OOM, "host allocation failed");
+  h->dom = *d;
+  h->dom.rho0 = rho0;
+  h->dom.nu_min = nu_min;
+  h->dom.nu_max = nu_max;
+  if (h->dom.check_interval <= 0) h->dom.check_interval = 100;
+  h->dtype = dtype;
+  h->elem = dtype == CLBM_F64 ? 8 : dtype == CLBM_F32 ? 4 : 2;
+  h->rsize = dtype == CLBM_F64 ? 8 : 4;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(nullptr, e, "cudaGetDevice");
+  }
+
+  Geom& g = h->g;
+  g.nx = d->nx;
+  g.ny = d->ny;
+  g.nz = d->nz;
+  g.pitch = int(round_up(d->nx, int64_t(128 / h->elem)));  // 128-byte rows
+  g.plane = int64_t(g.pitch) * g.ny;
+  g.qstride = round_up(g.plane * g.nz, 256);
+  g.facebits = 0;
+  for (int f = 0; f < 6; ++f) g.facebits |= unsigned(d->face[f]) << (2 * f);
+  for (int a = 0; a < 3; ++a) g.U[a] = U[a];
+  g.rho0 = rho0;
+  fill_params(h->P, K, n, body_force, rho0, nu_min, nu_max, dtype);
+  h->block.x = d->nx <= 32 ? 32 : d->nx <= 64 ? 64 : 128;
+  h->block.y = 128 / h->block.x;
+  h->block.z = 1;
+
+  auto cleanup = [&](int code, const std::string& m) {
+    g_create_err = m + (h->err.empty() ? "" : (": " + h->err));
+    clbm_destroy(h);
+    return code;
+  };
+  if (d->stream) {
+    h->stream = static_cast<cudaStream_t>(d->stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(CLBM_ERR_CUDA, cudaGetErrorString(e));
+    h->own_stream = true;
+  }
+  const size_t pop_bytes = size_t(NQ) * size_t(g.qstride) * h->elem;
+  for (int b = 0; b < 2; ++b) {
+    e = cudaMalloc(&h->buf[b], pop_bytes);
+    if (e != cudaSuccess) return cleanup(CLBM_ERR_OOM, "population buffer allocation failed");
+  }
+  e = cudaMalloc(&h->uprev, 3 * size_t(g.plane) * g.nz * h->rsize);
+  if (e != cudaSuccess) return cleanup(CLBM_ERR_OOM, "velocity buffer allocation failed");
+  e = cudaMalloc(&h->acc, 4 * sizeof(double));
+  if (e != cudaSuccess) return cleanup(CLBM_ERR_OOM, "reduction buffer allocation failed");
+  h->flag = reinterpret_cast<int*>(h->acc + 3);
+  e = cudaMallocHost(&h->host, 4 * sizeof(double));
+  if (e != cudaSuccess) return cleanup(CLBM_ERR_OOM, "pinned buffer allocation failed");
+  std::memset(h->host, 0, 4 * sizeof(double));
+  e = cudaEventCreateWithFlags(&h->check_done, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cleanup(CLBM_ERR_CUDA, cudaGetErrorString(e));
+  // Rest state: stored deviation f - w rho0 = 0 (all-zero bits in every form).
+  for (int b = 0; b < 2; ++b) {
+    e = cudaMemsetAsync(h->buf[b], 0, pop_bytes, h->stream);
+    if (e != cudaSuccess) return cleanup(CLBM_ERR_CUDA, cudaGetErrorString(e));
+  }
+  e = cudaMemsetAsync(h->uprev, 0, 3 * size_t(g.plane) * g.nz * h->rsize, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->acc, 0, 4 * sizeof(double), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cleanup(CLBM_ERR_CUDA, cudaGetErrorString(e));
+  *out = h;
+  return CLBM_OK;
+}
+
+int clbm_step(clbm_handle h, int64_t nsteps) {
+  if (bad(h)) return fail(h, CLBM_ERR_ARG, "invalid handle");
+  if (nsteps < 0) return fail(h, CLBM_ERR_ARG, "nsteps must be >= 0");
+  if (int r = set_device(h)) return r;
+  const int64_t every = h->dom.check_interval;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const bool check = ((h->steps + 1) % every) == 0;
+    if (check) CK(h, cudaMemsetAsync(h->acc, 0, 3 * sizeof(double), h->stream));
+    CK(h, dispatch_step(h, check));
+    h->cur = 1 - h->cur;
+    h->steps += 1;
+    if (check) {
+      h->checks += 1;
+      CK(h, cudaMemcpyAsync(h->host, h->acc, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+      CK(h, cudaEventRecord(h->check_done, h->stream));
+    }
+  }
+  if (!h->diverged && h->checks > 0 && cudaEventQuery(h->check_done) == cudaSuccess) {
+    int f = 0;
+    std::memcpy(&f, &h->host[3], sizeof(int));
+    h->diverged = f != 0;
+  }
+  if (h->diverged)
+    return fail(h, CLBM_ERR_DIVERGED, "divergence: non-finite value or density out of [0.5, 2]");
+  return CLBM_OK;
+}
+
+static int fields_impl(clbm_handle h, double* rho, double* u, double* gd) {
+  const void* src = h->buf[h->cur];
+  cudaError_t e;
+  switch (h->dtype) {
+    case CLBM_F64: e = launch_fields_f64(src, h->g, h->P, rho, u, gd, h->stream); break;
+    case CLBM_F32: e = launch_fields_f32(src, h->g, h->P, rho, u, gd, h->stream); break;
+    default: e = launch_fields_f16(src, h->g, h->P, rho, u, gd, h->stream); break;
+  }
+  CK(h, e);
+  return CLBM_OK;
+}
+
+int clbm_fields_device(clbm_handle h, double* rho, double* u, double* gamma_dot) {
+  if (bad(h)) return fail(h, CLBM_ERR_ARG, "invalid handle");
+  if (int r = set_device(h)) return r;
+  if (int r = fields_impl(h, rho, u, gamma_dot)) return r;
+  CK(h, cudaStreamSynchronize(h->stream));
+  return CLBM_OK;
+}
+
+int clbm_fields(clbm_handle h, double* rho, double* u, double* gamma_dot) {
+  if (bad(h)) return fail(h, CLBM_ERR_ARG, "invalid handle");
+  if (int r = set_device(h)) return r;
+  const size_t N = size_t(h->g.nx) * h->g.ny * h->g.nz;
+  double* dev = nullptr;
+  CK(h, cudaMallocAsync(reinterpret_cast<void**>(&dev), 5 * N * sizeof(double), h->stream));
+  int r = fields_impl(h, rho ? dev : nullptr, u ? dev + N : nullptr, gamma_dot ? dev + 4 * N : nullptr);
+  cudaError_t e = cudaSuccess;
+  if (r == CLBM_OK) {
+    if (rho) e = cudaMemcpyAsync(rho, dev, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (u && e == cudaSuccess)
+      e = cudaMemcpyAsync(u, dev + N, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (gamma_dot && e == cudaSuccess)
+      e = cudaMemcpyAsync(gamma_dot, dev + 4 * N, N * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream);
+  }
+  cudaFreeAsync(dev, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (r != CLBM_OK) return r;
+  CK(h, e);
+  return CLBM_OK;
+}
+
+int clbm_residual(clbm_handle h, double* out) {
+  if (bad(h) || !out) return fail(h, CLBM_ERR_ARG, "invalid handle or output");
+  if (int r = set_device(h)) return r;
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (h->checks < 2) {
+    *out = INFINITY;
+  } else if (!(h->host[1] > 0.0)) {
+    *out = h->host[0] == 0.0 ? 0.0 : INFINITY;   // fluid at rest
+  } else {
+    *out = std::sqrt(h->host[0]) / (double(h->dom.check_interval) * std::sqrt(h->host[1]));
+  }
+  int f = 0;
+  std::memcpy(&f, &h->host[3], sizeof(int));
+  h->diverged = h->diverged || f != 0;
+  if (h->diverged)
+    return fail(h, CLBM_ERR_DIVERGED, "divergence: non-finite value or density out of [0.5, 2]");
+  return CLBM_OK;
+}
+
+int clbm_mass(clbm_handle h, double* out) {
+  if (bad(h) || !out) return fail(h, CLBM_ERR_ARG, "invalid handle or output");
+  if (int r = set_device(h)) return r;
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (h->checks < 1) return fail(h, CLBM_ERR_ARG, "no check step has run yet");
+  const double N = double(h->g.nx) * h->g.ny * h->g.nz;
+  *out = N * h->g.rho0 + h->host[2];
+  return CLBM_OK;
+}
+
+static int state_io(clbm_handle h, double* out, const double* in) {
+  if (bad(h) || (!out && !in)) return fail(h, CLBM_ERR_ARG, "invalid handle or buffer");
+  if (int r = set_device(h)) return r;
+  const size_t n = size_t(h->g.nx) * h->g.ny * h->g.nz * NQ;
+  double* dev = nullptr;
+  CK(h, cudaMallocAsync(reinterpret_cast<void**>(&dev), n * sizeof(double), h->stream));
+  cudaError_t e = cudaSuccess;
+  const double isc = h->P.inv_scale;
+  if (in) {
+    e = cudaMemcpyAsync(dev, in, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+      switch (h->dtype) {
+        case CLBM_F64: e = launch_import_f64(dev, h->g, h->g.rho0, isc, h->buf[h->cur], h->stream); break;
+        case CLBM_F32: e = launch_import_f32(dev, h->g, h->g.rho0, isc, h->buf[h->cur], h->stream); break;
+        default: e = launch_import_f16(dev, h->g, h->g.rho0, isc, h->buf[h->cur], h->stream); break;
+      }
+    }
+  } else {
+    switch (h->dtype) {
+      case CLBM_F64: e = launch_export_f64(h->buf[h->cur], h->g, h->g.rho0, isc, dev, h->stream); break;
+      case CLBM_F32: e = launch_export_f32(h->buf[h->cur], h->g, h->g.rho0, isc, dev, h->stream); break;
+      default: e = launch_export_f16(h->buf[h->cur], h->g, h->g.rho0, isc, dev, h->stream); break;
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out, dev, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  }
+  cudaFreeAsync(dev, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  CK(h, e);
+  return CLBM_OK;
+}
+
+int clbm_get_state(clbm_handle h, double* f_host) { return state_io(h, f_host, nullptr); }
+int clbm_set_state(clbm_handle h, const double* f_host) {
+  if (!f_host) return fail(h, CLBM_ERR_ARG, "null state");
+  return state_io(h, nullptr, f_host);
+}
+
+int clbm_steps_done(clbm_handle h, int64_t* out) {
+  if (bad(h) || !out) return fail(h, CLBM_ERR_ARG, "invalid handle or output");
+  *out = h->steps;
+  return CLBM_OK;
+}
+
+int clbm_sync(clbm_handle h) {
+  if (bad(h)) return fail(h, CLBM_ERR_ARG, "invalid handle");
+  if (int r = set_device(h)) return r;
+  CK(h, cudaStreamSynchronize(h->stream));
+  return CLBM_OK;
+}
+
+int clbm_destroy(clbm_handle h) {
+  if (!h) return CLBM_OK;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int b = 0; b < 2; ++b)
+    if (h->buf[b]) cudaFree(h->buf[b]);
+  if (h->uprev) cudaFree(h->uprev);
+  if (h->acc) cudaFree(h->acc);
+  if (h->host) cudaFreeHost(h->host);
+  if (h->check_done) cudaEventDestroy(h->check_done);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return CLBM_OK;
+}
+
+const char* clbm_last_error(clbm_handle h) {
+  if (!h) return g_create_err.c_str();
+  return h->err.c_str();
+}
+
+int clbm_collide_nodes(clbm_dtype dtype, double K, double n, const double body_force[3],
+                       double rho0, double nu_min, double nu_max, const double* f_in,
+                       double* f_out, double* rho, double* u, double* gamma_dot, int64_t M) {
+  if (!f_in || !f_out || M <= 0) return fail(nullptr, CLBM_ERR_ARG, "bad node arrays");
+  if (dtype != CLBM_F64 && dtype != CLBM_F32 && dtype != CLBM_F16S)
+    return fail(nullptr, CLBM_ERR_ARG, "unknown dtype");
+  rho0 = rho0 > 0 ? rho0 : 1.0;
+  nu_min = nu_min > 0 ? nu_min : 5e-4;
+  nu_max = nu_max > 0 ? nu_max : 10.0;
+  std::string why;
+  if (!check_phys(K, n, nu_min, nu_max, why)) return fail(nullptr, CLBM_ERR_ARG, why);
+  PhysParams P{};
+  fill_params(P, K, n, body_force, rho0, nu_min, nu_max, dtype);
+  double* dev = nullptr;
+  const size_t bytes = size_t(M) * (19 + 19 + 1 + 3 + 1) * sizeof(double);
+  cudaError_t e = cudaMalloc(&dev, bytes);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaMalloc");
+  double* din = dev;
+  double* dout = dev + 19 * M;
+  double* drho = dout + 19 * M;
+  double* du = drho + M;
+  double* dgd = du + 3 * M;
+  e = cudaMemcpy(din, f_in, 19 * M * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    switch (dtype) {
+      case CLBM_F64: e = launch_collide_nodes_f64(P, din, dout, drho, du, dgd, M, 0); break;
+      case CLBM_F32: e = launch_collide_nodes_f32(P, din, dout, drho, du, dgd, M, 0); break;
+      default: e = launch_collide_nodes_f16(P, din, dout, drho, du, dgd, M, 0); break;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(f_out, dout, 19 * M * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && rho) e = cudaMemcpy(rho, drho, M * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && u) e = cudaMemcpy(u, du, 3 * M * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && gamma_dot)
+    e = cudaMemcpy(gamma_dot, dgd, M * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "clbm_collide_nodes");
+  return CLBM_OK;
+}
+
+}  // extern "C"

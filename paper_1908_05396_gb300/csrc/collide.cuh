@@ -1,0 +1,311 @@
+// collide.cuh -- cascaded central-moment collision of one node (Sec. 3),
+// written in deviation form d_a = f_a - w_a rho0.
+//
+// Working with deviations keeps the large rest-state constant out of every
+// sum: the raw moments of w rho0 are rho0 * (1, 0, 1/3, 0, 1/9) by order, so
+// each raw moment k' of f is that constant plus the same moment D of d, and
+// the constants cancel analytically in m^(1), in g^_4..g^_9 and in the
+// fourth-order attractor terms of g^_16..g^_18 (expanded around rho/3 below).
+// The FP32 and FP16-storage forms therefore lose no precision to a rest value
+// of order 1, and the FP64 form computes the same expressions.
+#pragma once
+
+#include "d3q19.cuh"
+
+namespace clbm {
+
+// Per-lattice constants of the collision, in the math precision R.
+template <typename R>
+struct CollideConst {
+  R rho0;
+  R F[3];        // body force
+  R K3;          // 3 K (K = mu_p, consistency coefficient, Eq. 5)
+  R logK3;       // log(3 K)
+  R n;           // power-law index
+  R ehalf;       // (n - 1) / 2
+  R ylo, yhi;    // log(3 nu_min), log(3 nu_max): clamp of y = log(1/w - 1/2)
+  R nu_min, nu_max;
+  int newtonian; // n == 1: omega_nu has a closed form
+  int has_force;
+};
+
+// Outputs of one collision besides the populations.
+template <typename R>
+struct NodeOut {
+  R rho, ux, uy, uz, gamma_dot;
+};
+
+template <typename R> __device__ __forceinline__ R rlog(R x);
+template <> __device__ __forceinline__ float rlog<float>(float x) { return __logf(x); }
+template <> __device__ __forceinline__ double rlog<double>(double x) { return log(x); }
+template <typename R> __device__ __forceinline__ R rexp(R x);
+template <> __device__ __forceinline__ float rexp<float>(float x) { return __expf(x); }
+template <> __device__ __forceinline__ double rexp<double>(double x) { return exp(x); }
+template <typename R> __device__ __forceinline__ R rdiv(R a, R b);
+template <> __device__ __forceinline__ float rdiv<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double rdiv<double>(double a, double b) { return a / b; }
+
+template <typename R> __device__ __forceinline__ R tiny();
+template <> __device__ __forceinline__ float tiny<float>() { return 1e-36f; }
+template <> __device__ __forceinline__ double tiny<double>() { return 1e-300; }
+
+// Newton iterations on y = log(1/omega - 1/2) for
+//   G(y) = y - log(3K/rho) - (n-1)/2 log(omega(y)^2 A + B) = 0,
+// i.e. 1/omega - 1/2 = 3 nu with nu = (K/rho) gamma_dot^(n-1) (Eq. 6,
+// Eq. localvarationsrelaxationtimes) and gamma_dot^2 = omega^2 A + B: the
+// omega part of the strain rate of Eq. strainratetensor is traceless, so its
+// invariant (Eq. shearrateexpression) is quadratic in omega.
+// dG/dy = 1 + (n-1) r tau omega with r = omega^2 A / gamma_dot^2 and
+// tau omega in (0, 1), so G is increasing with slope between min(n, 1) and
+// max(n, 1) and has one root; projecting each iterate onto [ylo, yhi] makes
+// the iteration land on the clamp when the root lies beyond it.
+template <typename R>
+__device__ __forceinline__ R newton_y(R y, R c, R ehalf, R nm1, R A, R B,
+                                      R ylo, R yhi, int iters) {
+#pragma unroll 1
+  for (int it = 0; it < iters; ++it) {
+    R tau = rexp<R>(y);
+    R w = R(1) / (tau + R(0.5));
+    R wwA = w * w * A;
+    R g2 = fmax(wwA + B, tiny<R>());
+    R G = y - c - ehalf * rlog<R>(g2);
+    R dG = R(1) + nm1 * rdiv<R>(wwA, g2) * (tau * w);
+    y = fmin(fmax(y - rdiv<R>(G, dG), ylo), yhi);
+  }
+  return y;
+}
+
+// omega_nu from A and B (see above); writes |gamma_dot| at that omega.
+template <typename R>
+__device__ __forceinline__ R omega_nu(const CollideConst<R>& C, R rho, R A,
+                                      R B, R* gd) {
+  R w;
+  if (C.newtonian) {
+    R nu = fmin(fmax(C.K3 / (R(3) * rho), C.nu_min), C.nu_max);
+    w = R(1) / (R(3) * nu + R(0.5));
+  } else {
+    // Four single-precision iterations from the guess omega = 2/3 reach the
+    // FP32 rounding level; the FP64 form polishes with two more in FP64.
+    float cf = float(C.logK3) - __logf(float(rho));
+    float Af = float(A), Bf = float(B);
+    float y0 = cf + float(C.ehalf) *
+                        __logf(fmaxf(Af * (4.0f / 9.0f) + Bf, 1e-36f));
+    y0 = fminf(fmaxf(y0, float(C.ylo)), float(C.yhi));
+    float yf = newton_y<float>(y0, cf, float(C.ehalf), float(C.n) - 1.0f, Af,
+                               Bf, float(C.ylo), float(C.yhi), 4);
+    R y = R(yf);
+    if (sizeof(R) == 8) {
+      R c = C.logK3 - rlog<R>(rho);
+      y = newton_y<R>(y, c, C.ehalf, C.n - R(1), A, B, C.ylo, C.yhi, 2);
+    }
+    w = R(1) / (rexp<R>(y) + R(0.5));
+  }
+  *gd = sqrt(fmax(w * w * A + B, R(0)));
+  return w;
+}
+
+// Collide one node.  d[19] holds the pre-collision deviations on entry and
+// the post-collision deviations f~ - w rho0 on return.
+template <typename R, bool FORCE>
+__device__ __forceinline__ void collide(const CollideConst<R>& C, R (&d)[Q],
+                                        NodeOut<R>& out) {
+  // ---- mass and momentum (Eqs. hydrodynamicfields1/2) -------------------
+  R s[NPAIR], t[NPAIR];
+#pragma unroll
+  for (int p = 0; p < NPAIR; ++p) {
+    s[p] = d[pair_pos(p)] + d[opp(pair_pos(p))];
+    t[p] = d[pair_pos(p)] - d[opp(pair_pos(p))];
+  }
+  R drho = d[0];
+  R jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+  for (int p = 0; p < NPAIR; ++p) {
+    const int q = pair_pos(p);
+    drho += s[p];
+    if (cx(q)) jx += R(cx(q)) * t[p];
+    if (cy(q)) jy += R(cy(q)) * t[p];
+    if (cz(q)) jz += R(cz(q)) * t[p];
+  }
+  const R rho = C.rho0 + drho;
+  const R rinv = R(1) / rho;
+  R ux, uy, uz;
+  if (FORCE) {
+    // Symmetric split of the body force: the velocity is (j + F/2)/rho and
+    // half of the source S_a = w_a [3 e.F + 9 (e.u)(e.F) - 3 u.F] is added
+    // before the collision (its moments are 0, F and uF + Fu).
+    ux = (jx + R(0.5) * C.F[0]) * rinv;
+    uy = (jy + R(0.5) * C.F[1]) * rinv;
+    uz = (jz + R(0.5) * C.F[2]) * rinv;
+  } else {
+    ux = jx * rinv;
+    uy = jy * rinv;
+    uz = jz * rinv;
+  }
+  R Sa[FORCE ? Q : 1];
+  if (FORCE) {
+    const R uF = ux * C.F[0] + uy * C.F[1] + uz * C.F[2];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      R eF = R(cx(q)) * C.F[0] + R(cy(q)) * C.F[1] + R(cz(q)) * C.F[2];
+      R eu = R(cx(q)) * ux + R(cy(q)) * uy + R(cz(q)) * uz;
+      Sa[q] = wt<R>(q) * (R(3) * eF + R(9) * eu * eF - R(3) * uF);
+      d[q] += R(0.5) * Sa[q];
+    }
+#pragma unroll
+    for (int p = 0; p < NPAIR; ++p) {
+      s[p] = d[pair_pos(p)] + d[opp(pair_pos(p))];
+      t[p] = d[pair_pos(p)] - d[opp(pair_pos(p))];
+    }
+  }
+
+  // ---- raw moments of the deviations (Eq. rawmomentdistributionfunction1)
+  // k'_ii = rho0/3 + Dii, k'_ij = Dij, third order k' = D, k'_iijj = rho0/9 + D.
+  R Dxx = 0, Dyy = 0, Dzz = 0, Dxy = 0, Dxz = 0, Dyz = 0;
+  R Dxyy = 0, Dxzz = 0, Dxxy = 0, Dyzz = 0, Dxxz = 0, Dyyz = 0;
+  R Dxxyy = 0, Dxxzz = 0, Dyyzz = 0;
+#pragma unroll
+  for (int p = 0; p < NPAIR; ++p) {
+    const int q = pair_pos(p);
+    const int x = cx(q), y = cy(q), z = cz(q);
+    if (x * x) Dxx += s[p];
+    if (y * y) Dyy += s[p];
+    if (z * z) Dzz += s[p];
+    if (x * y) Dxy += R(x * y) * s[p];
+    if (x * z) Dxz += R(x * z) * s[p];
+    if (y * z) Dyz += R(y * z) * s[p];
+    if (x * y * y) Dxyy += R(x * y * y) * t[p];
+    if (x * z * z) Dxzz += R(x * z * z) * t[p];
+    if (x * x * y) Dxxy += R(x * x * y) * t[p];
+    if (y * z * z) Dyzz += R(y * z * z) * t[p];
+    if (x * x * z) Dxxz += R(x * x * z) * t[p];
+    if (y * y * z) Dyyz += R(y * y * z) * t[p];
+    if (x * x * y * y) Dxxyy += s[p];
+    if (x * x * z * z) Dxxzz += s[p];
+    if (y * y * z * z) Dyyzz += s[p];
+  }
+
+  const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
+  const R r3 = C.rho0 * R(1.0 / 3.0);
+  const R kxx = r3 + Dxx, kyy = r3 + Dyy, kzz = r3 + Dzz;
+
+  // ---- non-equilibrium second moments m^(1)_4..9 (Sec. 3.2) -------------
+  const R m4 = Dxy - rho * ux * uy;
+  const R m5 = Dxz - rho * ux * uz;
+  const R m6 = Dyz - rho * uy * uz;
+  const R m7 = (Dxx - Dyy) - rho * (ux2 - uy2);
+  const R m8 = (Dxx - Dzz) - rho * (ux2 - uz2);
+  const R m9 = (Dxx + Dyy + Dzz) - drho - rho * (ux2 + uy2 + uz2);
+
+  // gamma_dot^2 = omega^2 A + B from Eq. strainratetensor (omega_zeta = 1):
+  // with q = 1/(2 rho), the traceless part gives
+  // A = 12 q^2 [m7^2 - m7 m8 + m8^2 + 3 (m4^2 + m5^2 + m6^2)], B = 6 q^2 m9^2.
+  const R q2 = R(0.25) * rinv * rinv;
+  const R A = R(12) * q2 * (m7 * m7 - m7 * m8 + m8 * m8 + R(3) * (m4 * m4 + m5 * m5 + m6 * m6));
+  const R B = R(6) * q2 * m9 * m9;
+  R gd;
+  const R w = omega_nu<R>(C, rho, A, B, &gd);
+
+  // ---- change of moments, Eqs. collisionkernelg4..g18 --------------------
+  // omega_4..8 = w, omega_9..18 = 1 (Sec. 3.1).
+  const R g4 = R(-0.25) * w * m4;
+  const R g5 = R(-0.25) * w * m5;
+  const R g6 = R(-0.25) * w * m6;
+  const R g7 = R(-1.0 / 12.0) * w * m7;
+  const R g8 = R(-1.0 / 36.0) * w * (R(2) * m8 - m7);
+  const R g9 = R(-1.0 / 126.0) * m9;
+
+  const R g10 = R(0.125) * (-(Dxyy + Dxzz) + R(2) * (uy * Dxy + uz * Dxz) + ux * (kyy + kzz) -
+                            R(2) * rho * ux * (uy2 + uz2)) +
+                (uy * g4 + uz * g5) + R(0.75) * ux * (-(g7 + g8) + R(14) * g9);
+  const R g11 = R(0.125) * (-(Dyzz + Dxxy) + R(2) * (ux * Dxy + uz * Dyz) + uy * (kxx + kzz) -
+                            R(2) * rho * uy * (ux2 + uz2)) +
+                (ux * g4 + uz * g6) + R(0.75) * uy * (g7 - g8 + R(14) * g9);
+  const R g12 = R(0.125) * (-(Dxxz + Dyyz) + R(2) * (ux * Dxz + uy * Dyz) + uz * (kxx + kyy) -
+                            R(2) * rho * uz * (ux2 + uy2)) +
+                (ux * g5 + uy * g6) + R(1.5) * uz * (g8 + R(7) * g9);
+  const R g13 = R(0.125) * (-(Dxyy - Dxzz) + R(2) * (uy * Dxy - uz * Dxz) + ux * (Dyy - Dzz) -
+                            R(2) * rho * ux * (uy2 - uz2)) +
+                (uy * g4 - uz * g5) + R(0.75) * ux * (-g7 + R(3) * g8);
+  const R g14 = R(0.125) * (-(Dyzz - Dxxy) + R(2) * (uz * Dyz - ux * Dxy) + uy * (Dzz - Dxx) -
+                            R(2) * rho * uy * (uz2 - ux2)) +
+                (-ux * g4 + uz * g6) + R(0.75) * uy * (-g7 - R(3) * g8);
+  const R g15 = R(0.125) * (-(Dxxz - Dyyz) + R(2) * (ux * Dxz - uy * Dyz) + uz * (Dxx - Dyy) -
+                            R(2) * rho * uz * (ux2 - uy2)) +
+                (ux * g5 - uy * g6) + R(1.5) * uz * g7;
+
+  // Post-collision diagonal central moments k~ii = rho/3 + a_i (the <K g^|e_i^2>
+  // rows of Eq. momentscascadedcollisionterm added to k'_ii - rho u_i^2), and
+  // the factorised attractors k~ii k~jj / rho expanded around rho/3, so that
+  // the rho0/9 of the raw fourth moments cancels analytically.
+  const R third = R(1.0 / 3.0);
+  const R ax = Dxx - third * drho - rho * ux2 + R(6) * g7 + R(6) * g8 + R(42) * g9;
+  const R ay = Dyy - third * drho - rho * uy2 - R(6) * g7 + R(6) * g8 + R(42) * g9;
+  const R az = Dzz - third * drho - rho * uz2 - R(12) * g8 + R(42) * g9;
+
+  const R b16 = third * drho - (Dxxyy + Dxxzz + Dyyzz) + R(2.0 / 3.0) * (ax + ay + az) +
+                (ax * ay + ax * az + ay * az) * rinv + R(2) * ux * (Dxyy + Dxzz) +
+                R(2) * uy * (Dxxy + Dyzz) + R(2) * uz * (Dxxz + Dyyz) - ux2 * (kyy + kzz) -
+                uy2 * (kzz + kxx) - uz2 * (kxx + kyy) -
+                R(4) * (ux * uy * Dxy + ux * uz * Dxz + uy * uz * Dyz) +
+                R(3) * rho * (ux2 * uy2 + ux2 * uz2 + uy2 * uz2);
+  const R g16 = R(1.0 / 12.0) * b16 - R(4.0 / 3.0) * (ux * uy * g4 + ux * uz * g5 + uy * uz * g6) +
+                R(0.5) * (ux2 - uy2) * g7 + R(0.5) * (ux2 + uy2 - R(2) * uz2) * g8 +
+                (R(-7) * (ux2 + uy2 + uz2) - R(8)) * g9 +
+                R(4.0 / 3.0) * (ux * g10 + uy * g11 + uz * g12);
+
+  const R b17 = -(Dxxyy + Dxxzz - R(2) * Dyyzz) + third * (R(2) * ax - ay - az) +
+                (ax * ay + ax * az - R(2) * ay * az) * rinv +
+                R(2) * ((ux * Dxyy + ux * Dxzz + uy * Dxxy + uz * Dxxz) - R(2) * (uy * Dyzz + uz * Dyyz)) -
+                ux2 * (kyy + kzz) - uy2 * (kxx - R(2) * kzz) - uz2 * (kxx - R(2) * kyy) -
+                R(4) * (ux * uy * Dxy + ux * uz * Dxz - R(2) * uy * uz * Dyz) +
+                R(3) * rho * (ux2 * uy2 + ux2 * uz2 - R(2) * uy2 * uz2);
+  const R g17 = R(1.0 / 24.0) * b17 - R(2.0 / 3.0) * (ux * uy * g4 + ux * uz * g5) +
+                R(4.0 / 3.0) * uy * uz * g6 + R(0.25) * (ux2 - uy2 - R(3) * uz2 - R(2)) * g7 +
+                R(0.25) * (ux2 - R(5) * uy2 + uz2 - R(2)) * g8 +
+                R(1.75) * (R(-2) * ux2 + uy2 + uz2) * g9 + R(2.0 / 3.0) * ux * g10 -
+                third * (uy * g11 + uz * g12) - uy * g14 + uz * g15;
+
+  const R b18 = -(Dxxyy - Dxxzz) + third * (ay - az) + ax * (ay - az) * rinv +
+                R(2) * (ux * (Dxyy - Dxzz) + uy * Dxxy - uz * Dxxz) - ux2 * (Dyy - Dzz) +
+                (uz2 - uy2) * kxx - R(4) * (ux * uy * Dxy - ux * uz * Dxz) +
+                R(3) * rho * (ux2 * uy2 - ux2 * uz2);
+  const R g18 = R(0.125) * b18 - R(2) * ux * uy * g4 + R(2) * ux * uz * g5 +
+                R(0.75) * (ux2 - uy2 + uz2 + R(2.0 / 3.0)) * g7 +
+                R(0.75) * (R(-3) * ux2 - uy2 + uz2 - R(2)) * g8 + R(5.25) * (uz2 - uy2) * g9 +
+                uy * g11 - uz * g12 + R(2) * ux * g13 - uy * g14 - uz * g15;
+
+  // ---- back-transform f~ = f + K g^ (+ second half of the source) --------
+  // Even basis vectors take the same value at e and -e, odd ones flip sign,
+  // so each +/- pair shares its even part E and odd part O.
+  const R g[Q] = {R(0), R(0), R(0), R(0), g4,  g5,  g6,  g7,  g8, g9,
+                  g10,  g11,  g12,  g13,  g14, g15, g16, g17, g18};
+  d[0] += R(kb(9, 0, 0, 0)) * g9 + R(kb(16, 0, 0, 0)) * g16;
+#pragma unroll
+  for (int p = 0; p < NPAIR; ++p) {
+    const int q = pair_pos(p);
+    const int x = cx(q), y = cy(q), z = cz(q);
+    R E = R(0), O = R(0);
+#pragma unroll
+    for (int j = 4; j < Q; ++j) {
+      const int k = kb(j, x, y, z);
+      if (k == 0) continue;
+      if (kb_odd(j))
+        O += R(k) * g[j];
+      else
+        E += R(k) * g[j];
+    }
+    d[q] += E + O;
+    d[opp(q)] += E - O;
+  }
+  if (FORCE) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) d[q] += R(0.5) * Sa[q];
+  }
+  out.rho = rho;
+  out.ux = ux;
+  out.uy = uy;
+  out.uz = uz;
+  out.gamma_dot = gd;
+}
+
+}  // namespace clbm

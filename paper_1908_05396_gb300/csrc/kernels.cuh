@@ -1,0 +1,351 @@
+// kernels.cuh -- fused pull-stream + cascaded-collision step and its helpers.
+//
+// Storage: structure of arrays pop[q][z][y][x] with a padded row pitch, two
+// buffers (A-B).  A thread owns one node: it pulls the 19 post-collision
+// populations of its upwind neighbours from buffer A (Eq. cascadedstreaming1),
+// resolving walls, the lid and periodic faces from its own index, collides
+// (Sec. 3) and writes the 19 results to its own slot of buffer B.  Every
+// read and write of a warp covers consecutive x, so the accesses coalesce;
+// the +/-x directions are offset by one element, which costs one extra
+// sector per warp in L1/L2 but no extra DRAM traffic.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "collide.cuh"
+#include "launch.h"
+
+namespace clbm {
+
+// ---- storage codecs: stored value <-> deviation f - w rho0 -----------------
+template <typename S, typename R> struct Codec;
+template <typename R> struct Codec<double, R> {
+  static __device__ __forceinline__ R dec(double v, R) { return R(v); }
+  static __device__ __forceinline__ double enc(R v, R) { return double(v); }
+};
+template <typename R> struct Codec<float, R> {
+  static __device__ __forceinline__ R dec(float v, R) { return R(v); }
+  static __device__ __forceinline__ float enc(R v, R) { return float(v); }
+};
+template <typename R> struct Codec<__half, R> {
+  // (f - w rho0) * 1024 in FP16, round to nearest even.  The power-of-two
+  // scale is exact and lifts deviations down to ~6e-8 out of the FP16
+  // subnormal range while keeping |f - w rho0| < 64 representable.
+  static __device__ __forceinline__ R dec(__half v, R) {
+    return R(__half2float(v)) * R(1.0 / F16_SCALE);
+  }
+  static __device__ __forceinline__ __half enc(R v, R) {
+    return __float2half_rn(float(v) * float(F16_SCALE));
+  }
+};
+
+template <typename R>
+__device__ __forceinline__ CollideConst<R> make_const(const PhysParams& P) {
+  CollideConst<R> C;
+  C.rho0 = R(P.rho0);
+  C.F[0] = R(P.F[0]);
+  C.F[1] = R(P.F[1]);
+  C.F[2] = R(P.F[2]);
+  C.K3 = R(3.0 * P.K);
+  C.logK3 = R(P.logK3);
+  C.n = R(P.n);
+  C.ehalf = R(0.5 * (P.n - 1.0));
+  C.ylo = R(P.ylo);
+  C.yhi = R(P.yhi);
+  C.nu_min = R(P.nu_min);
+  C.nu_max = R(P.nu_max);
+  C.newtonian = P.newtonian;
+  C.has_force = P.has_force;
+  return C;
+}
+
+// Pull the 19 pre-collision deviations of node (x, y, z).
+template <typename S, typename R>
+__device__ __forceinline__ void pull(const S* __restrict__ src, const Geom& g,
+                                     int x, int y, int z, int64_t i, R inv_scale,
+                                     R (&d)[Q]) {
+  const bool interior = x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 &&
+                        z > 0 && z < g.nz - 1;
+  if (interior) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int64_t off = int64_t(cz(q)) * g.plane + int64_t(cy(q)) * g.pitch + cx(q);
+      d[q] = Codec<S, R>::dec(src[q * g.qstride + i - off], inv_scale);
+    }
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    int s[3] = {x - cx(q), y - cy(q), z - cz(q)};
+    const int n3[3] = {g.nx, g.ny, g.nz};
+    bool bounce = false, lid = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (s[a] < 0 || s[a] >= n3[a]) {
+        const int kind = (g.facebits >> (2 * (2 * a + (s[a] < 0 ? 0 : 1)))) & 3;
+        if (kind == BC_PERIODIC) {
+          s[a] += (s[a] < 0) ? n3[a] : -n3[a];
+        } else {
+          bounce = true;
+          lid = lid || kind == BC_LID;
+        }
+      }
+    }
+    if (bounce) {
+      // Halfway bounce-back f_q(x) = f~_opp(q)(x); a lid adds
+      // 6 w_q rho0 (e_q . U), which is the same for deviations.
+      R v = Codec<S, R>::dec(src[opp(q) * g.qstride + i], inv_scale);
+      if (lid)
+        v += R(6) * wt<R>(q) * R(g.rho0) *
+             (R(cx(q)) * R(g.U[0]) + R(cy(q)) * R(g.U[1]) + R(cz(q)) * R(g.U[2]));
+      d[q] = v;
+    } else {
+      const int64_t j = int64_t(s[2]) * g.plane + int64_t(s[1]) * g.pitch + s[0];
+      d[q] = Codec<S, R>::dec(src[q * g.qstride + j], inv_scale);
+    }
+  }
+}
+
+// Block-wide FP64 sum of v, added atomically to *acc by one thread.
+__device__ __forceinline__ void block_sum_add(double v, double* acc, double* smem) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+  const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  const int nwarp = (blockDim.x * blockDim.y + 31) >> 5;
+  if (lane == 0) smem[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = (lane < nwarp) ? smem[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) atomicAdd(acc, v);
+  }
+  __syncthreads();
+}
+
+// One time step.  CHECK = true also writes u into uprev (after reading the
+// previous check's value there) and reduces sum|u - uprev|^2, sum|u|^2,
+// sum(rho - rho0) and a divergence flag in FP64.
+template <typename S, typename R, bool FORCE, bool CHECK>
+__global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ src,
+                                                   S* __restrict__ dst, Geom g,
+                                                   PhysParams P, CheckBufs cb) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  const bool active = x < g.nx && y < g.ny;
+  if (!CHECK && !active) return;
+  const R inv_scale = R(P.inv_scale);
+  const CollideConst<R> C = make_const<R>(P);
+  double du2 = 0.0, uu = 0.0, dr = 0.0;
+  int bad = 0;
+  if (active) {
+    const int64_t i = int64_t(z) * g.plane + int64_t(y) * g.pitch + x;
+    R d[Q];
+    pull<S, R>(src, g, x, y, z, i, inv_scale, d);
+    NodeOut<R> o;
+    collide<R, FORCE>(C, d, o);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) dst[q * g.qstride + i] = Codec<S, R>::enc(d[q], inv_scale);
+    if (CHECK) {
+      R* up = reinterpret_cast<R*>(cb.uprev);
+      const int64_t nst = g.plane * g.nz;
+      const R px = up[i], py = up[nst + i], pz = up[2 * nst + i];
+      up[i] = o.ux;
+      up[nst + i] = o.uy;
+      up[2 * nst + i] = o.uz;
+      const double ex = double(o.ux) - double(px), ey = double(o.uy) - double(py),
+                   ez = double(o.uz) - double(pz);
+      du2 = ex * ex + ey * ey + ez * ez;
+      uu = double(o.ux) * double(o.ux) + double(o.uy) * double(o.uy) +
+           double(o.uz) * double(o.uz);
+      dr = double(o.rho) - double(P.rho0);
+      const double chk = double(o.rho) + double(o.ux) + double(o.uy) + double(o.uz);
+      bad = !(chk == chk) || !(fabs(chk) < 1e30) || !(double(o.rho) > 0.5 && double(o.rho) < 2.0);
+    }
+  }
+  if (CHECK) {
+    __shared__ double smem[32];
+    block_sum_add(du2, &cb.acc[0], smem);
+    block_sum_add(uu, &cb.acc[1], smem);
+    block_sum_add(dr, &cb.acc[2], smem);
+    if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(cb.flag, 1);
+  }
+}
+
+// Macroscopic fields of the current state (pull + moments + omega solve).
+template <typename S, typename R, bool FORCE>
+__global__ void __launch_bounds__(256) fields_kernel(const S* __restrict__ src, Geom g,
+                                                     PhysParams P, double* rho,
+                                                     double* u, double* gd) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return;
+  const R inv_scale = R(P.inv_scale);
+  const CollideConst<R> C = make_const<R>(P);
+  const int64_t i = int64_t(z) * g.plane + int64_t(y) * g.pitch + x;
+  R d[Q];
+  pull<S, R>(src, g, x, y, z, i, inv_scale, d);
+  NodeOut<R> o;
+  collide<R, FORCE>(C, d, o);
+  const int64_t N = int64_t(g.nx) * g.ny * g.nz;
+  const int64_t k = (int64_t(z) * g.ny + y) * g.nx + x;
+  if (rho) rho[k] = double(o.rho);
+  if (u) {
+    u[k] = double(o.ux);
+    u[N + k] = double(o.uy);
+    u[2 * N + k] = double(o.uz);
+  }
+  if (gd) gd[k] = double(o.gamma_dot);
+}
+
+// Collide M independent nodes given as plain FP64 populations [q][node].
+template <typename S, typename R, bool FORCE>
+__global__ void collide_nodes_kernel(PhysParams P, const double* __restrict__ fin,
+                                     double* __restrict__ fout, double* rho,
+                                     double* u, double* gd, int64_t M) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= M) return;
+  const R inv_scale = R(P.inv_scale);
+  const CollideConst<R> C = make_const<R>(P);
+  R d[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const R dev = R(fin[q * M + k] - wt<double>(q) * P.rho0);
+    d[q] = Codec<S, R>::dec(Codec<S, R>::enc(dev, inv_scale), inv_scale);
+  }
+  NodeOut<R> o;
+  collide<R, FORCE>(C, d, o);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const R st = Codec<S, R>::dec(Codec<S, R>::enc(d[q], inv_scale), inv_scale);
+    fout[q * M + k] = double(st) + wt<double>(q) * P.rho0;
+  }
+  if (rho) rho[k] = double(o.rho);
+  if (u) {
+    u[k] = double(o.ux);
+    u[M + k] = double(o.uy);
+    u[2 * M + k] = double(o.uz);
+  }
+  if (gd) gd[k] = double(o.gamma_dot);
+}
+
+// Stored populations <-> plain FP64 f in the unpadded layout [q][z][y][x].
+template <typename S>
+__global__ void export_kernel(const S* __restrict__ src, Geom g, double rho0,
+                              double inv_scale, double* __restrict__ out) {
+  const int64_t N = int64_t(g.nx) * g.ny * g.nz;
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= N * Q) return;
+  const int q = int(t / N);
+  const int64_t k = t - int64_t(q) * N;
+  const int x = int(k % g.nx), y = int((k / g.nx) % g.ny), z = int(k / (int64_t(g.nx) * g.ny));
+  const int64_t i = int64_t(z) * g.plane + int64_t(y) * g.pitch + x;
+  const double w = wt<double>(q);
+  out[t] = double(Codec<S, double>::dec(src[q * g.qstride + i], inv_scale)) + w * rho0;
+}
+
+template <typename S>
+__global__ void import_kernel(const double* __restrict__ in, Geom g, double rho0,
+                              double inv_scale, S* __restrict__ dst) {
+  const int64_t N = int64_t(g.nx) * g.ny * g.nz;
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= N * Q) return;
+  const int q = int(t / N);
+  const int64_t k = t - int64_t(q) * N;
+  const int x = int(k % g.nx), y = int((k / g.nx) % g.ny), z = int(k / (int64_t(g.nx) * g.ny));
+  const int64_t i = int64_t(z) * g.plane + int64_t(y) * g.pitch + x;
+  const double w = wt<double>(q);
+  dst[q * g.qstride + i] = Codec<S, double>::enc(in[t] - w * rho0, inv_scale);
+}
+
+// ---- host-side launchers, instantiated once per storage type --------------
+template <typename S, typename R>
+cudaError_t launch_step_t(const void* src, void* dst, const Geom& g, const PhysParams& P,
+                          const CheckBufs& cb, bool check, dim3 block, cudaStream_t st) {
+  dim3 grid((g.nx + block.x - 1) / block.x, (g.ny + block.y - 1) / block.y, g.nz);
+  const S* s = static_cast<const S*>(src);
+  S* d = static_cast<S*>(dst);
+  if (P.has_force) {
+    if (check) step_kernel<S, R, true, true><<<grid, block, 0, st>>>(s, d, g, P, cb);
+    else step_kernel<S, R, true, false><<<grid, block, 0, st>>>(s, d, g, P, cb);
+  } else {
+    if (check) step_kernel<S, R, false, true><<<grid, block, 0, st>>>(s, d, g, P, cb);
+    else step_kernel<S, R, false, false><<<grid, block, 0, st>>>(s, d, g, P, cb);
+  }
+  return cudaGetLastError();
+}
+
+template <typename S, typename R>
+cudaError_t launch_fields_t(const void* src, const Geom& g, const PhysParams& P, double* rho,
+                            double* u, double* gd, cudaStream_t st) {
+  dim3 block(32, 4);
+  dim3 grid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz);
+  const S* s = static_cast<const S*>(src);
+  if (P.has_force) fields_kernel<S, R, true><<<grid, block, 0, st>>>(s, g, P, rho, u, gd);
+  else fields_kernel<S, R, false><<<grid, block, 0, st>>>(s, g, P, rho, u, gd);
+  return cudaGetLastError();
+}
+
+template <typename S, typename R>
+cudaError_t launch_collide_nodes_t(const PhysParams& P, const double* fin, double* fout,
+                                   double* rho, double* u, double* gd, int64_t M,
+                                   cudaStream_t st) {
+  const int b = 128;
+  const unsigned grid = unsigned((M + b - 1) / b);
+  if (P.has_force) collide_nodes_kernel<S, R, true><<<grid, b, 0, st>>>(P, fin, fout, rho, u, gd, M);
+  else collide_nodes_kernel<S, R, false><<<grid, b, 0, st>>>(P, fin, fout, rho, u, gd, M);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_export_t(const void* src, const Geom& g, double rho0, double inv_scale,
+                            double* out, cudaStream_t st) {
+  const int64_t total = int64_t(g.nx) * g.ny * g.nz * Q;
+  const int b = 256;
+  export_kernel<S><<<unsigned((total + b - 1) / b), b, 0, st>>>(static_cast<const S*>(src), g,
+                                                                 rho0, inv_scale, out);
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_import_t(const double* in, const Geom& g, double rho0, double inv_scale,
+                            void* dst, cudaStream_t st) {
+  const int64_t total = int64_t(g.nx) * g.ny * g.nz * Q;
+  const int b = 256;
+  import_kernel<S><<<unsigned((total + b - 1) / b), b, 0, st>>>(in, g, rho0, inv_scale,
+                                                                 static_cast<S*>(dst));
+  return cudaGetLastError();
+}
+
+}  // namespace clbm
+
+// Defines the launchers of launch.h for one storage type S with math type R.
+#define CLBM_DEFINE_LAUNCHERS(SUFFIX, S, R)                                                   \
+  namespace clbm {                                                                            \
+  cudaError_t launch_step_##SUFFIX(const void* src, void* dst, const Geom& g,                 \
+                                   const PhysParams& P, const CheckBufs& cb, bool check,      \
+                                   dim3 block, cudaStream_t st) {                             \
+    return launch_step_t<S, R>(src, dst, g, P, cb, check, block, st);                         \
+  }                                                                                           \
+  cudaError_t launch_fields_##SUFFIX(const void* src, const Geom& g, const PhysParams& P,     \
+                                     double* rho, double* u, double* gd, cudaStream_t st) {   \
+    return launch_fields_t<S, R>(src, g, P, rho, u, gd, st);                                  \
+  }                                                                                           \
+  cudaError_t launch_collide_nodes_##SUFFIX(const PhysParams& P, const double* fin,           \
+                                            double* fout, double* rho, double* u, double* gd, \
+                                            int64_t M, cudaStream_t st) {                     \
+    return launch_collide_nodes_t<S, R>(P, fin, fout, rho, u, gd, M, st);                     \
+  }                                                                                           \
+  cudaError_t launch_export_##SUFFIX(const void* src, const Geom& g, double rho0,             \
+                                     double inv_scale, double* out, cudaStream_t st) {        \
+    return launch_export_t<S>(src, g, rho0, inv_scale, out, st);                              \
+  }                                                                                           \
+  cudaError_t launch_import_##SUFFIX(const double* in, const Geom& g, double rho0,            \
+                                     double inv_scale, void* dst, cudaStream_t st) {          \
+    return launch_import_t<S>(in, g, rho0, inv_scale, dst, st);                               \
+  }                                                                                           \
+  }

@@ -1,0 +1,65 @@
+// launch.h -- internal interface between the host library and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace clbm {
+
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_LID = 2 };
+constexpr int NQ = 19;  // D3Q19 directions
+enum { DT_F64 = 0, DT_F32 = 1, DT_F16S = 2 };
+
+// Power-of-two scale of the FP16 shifted storage: stored = (f - w rho0) * 1024.
+constexpr double F16_SCALE = 1024.0;
+
+// Lattice geometry and the stored layout pop[q][z][y][x] with row pitch.
+struct Geom {
+  int nx, ny, nz;
+  int pitch;        // elements per stored row, >= nx
+  int64_t plane;    // pitch * ny
+  int64_t qstride;  // elements per direction array, >= plane * nz
+  unsigned facebits; // 2 bits per face (BC_*), faces -x, +x, -y, +y, -z, +z
+  double U[3];      // lid velocity
+  double rho0;
+};
+
+// Physical parameters of the collision (host precision; kernels convert).
+struct PhysParams {
+  double rho0;
+  double F[3];
+  double K, logK3, n;
+  double ylo, yhi;  // log(3 nu_min), log(3 nu_max)
+  double nu_min, nu_max;
+  double inv_scale; // storage decode scale (1 except FP16)
+  int newtonian;
+  int has_force;
+};
+
+// Work buffers of a check step.
+struct CheckBufs {
+  void* uprev;      // 3 x (plane * nz) velocities of the previous check, math type
+  double* acc;      // [0] sum|u-uprev|^2, [1] sum|u|^2, [2] sum(rho - rho0)
+  int* flag;        // divergence flag
+};
+
+// Launchers, one instantiation per storage type (one translation unit each).
+#define CLBM_DECLARE_LAUNCHERS(SUFFIX)                                                        \
+  cudaError_t launch_step_##SUFFIX(const void* src, void* dst, const Geom& g,                 \
+                                   const PhysParams& P, const CheckBufs& cb, bool check,      \
+                                   dim3 block, cudaStream_t st);                              \
+  cudaError_t launch_fields_##SUFFIX(const void* src, const Geom& g, const PhysParams& P,     \
+                                     double* rho, double* u, double* gd, cudaStream_t st);    \
+  cudaError_t launch_collide_nodes_##SUFFIX(const PhysParams& P, const double* fin,           \
+                                            double* fout, double* rho, double* u, double* gd, \
+                                            int64_t M, cudaStream_t st);                      \
+  cudaError_t launch_export_##SUFFIX(const void* src, const Geom& g, double rho0,             \
+                                     double inv_scale, double* out, cudaStream_t st);         \
+  cudaError_t launch_import_##SUFFIX(const double* in, const Geom& g, double rho0,            \
+                                     double inv_scale, void* dst, cudaStream_t st);
+
+CLBM_DECLARE_LAUNCHERS(f64)
+CLBM_DECLARE_LAUNCHERS(f32)
+CLBM_DECLARE_LAUNCHERS(f16)
+
+}  // namespace clbm

@@ -1,0 +1,4 @@
+// step_f16.cu -- kernels of the f16 storage form (__half storage, float collision).
+#include "kernels.cuh"
+
+CLBM_DEFINE_LAUNCHERS(f16, __half, float)

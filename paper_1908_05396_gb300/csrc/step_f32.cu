@@ -1,0 +1,4 @@
+// step_f32.cu -- kernels of the f32 storage form (float storage, float collision).
+#include "kernels.cuh"
+
+CLBM_DEFINE_LAUNCHERS(f32, float, float)

@@ -1,0 +1,76 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry
+point that ``include/clbm.h`` declares, and rejects invalid arguments before
+touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def clbm():
+    from paper_1908_05396_gb300 import build
+    build.build()
+    from paper_1908_05396_gb300 import clbm as c
+    c.lib()
+    return c
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:int|const char\*|void)\s+(clbm_\w+)\s*\(", txt, re.M))
+    return names
+
+
+def test_every_declared_symbol_is_exported(clbm):
+    names = _declared()
+    assert {"clbm_create", "clbm_step", "clbm_fields", "clbm_residual", "clbm_destroy"} <= names
+    L = clbm.lib()
+    for n in sorted(names):
+        assert hasattr(L, n), n
+
+
+def _create(clbm, **kw):
+    d = clbm.Domain()
+    d.nx, d.ny, d.nz = kw.get("dims", (4, 4, 4))
+    for i, f in enumerate(kw.get("face", (0,) * 6)):
+        d.face[i] = f
+    h = ctypes.c_void_p()
+    U = kw.get("U")
+    Uc = (ctypes.c_double * 3)(*U) if U is not None else None
+    rc = clbm.lib().clbm_create(ctypes.byref(d), kw.get("K", 0.1), kw.get("n", 1.0), Uc, None,
+                                kw.get("dtype", 0), ctypes.byref(h))
+    return rc, clbm.lib().clbm_last_error(None).decode()
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(dims=(0, 4, 4)), "dimensions"),
+    (dict(K=-1.0), "K must"),
+    (dict(K=float("nan")), "K must"),
+    (dict(n=0.0), "n must"),
+    (dict(n=3.5), "n must"),
+    (dict(dtype=7), "dtype"),
+    (dict(face=(0, 1, 0, 0, 0, 0)), "periodic"),
+    (dict(face=(0, 0, 1, 2, 0, 0)), "without U_lid"),
+    (dict(face=(0, 0, 1, 2, 0, 0), U=(0.4, 0, 0)), "< 0.3"),
+    (dict(face=(0, 0, 1, 2, 0, 0), U=(0, 0.05, 0)), "tangential"),
+    (dict(face=(0, 0, 5, 1, 0, 0)), "face kind"),
+])
+def test_create_rejects_bad_arguments(clbm, kw, frag):
+    rc, msg = _create(clbm, **kw)
+    assert rc == clbm.ERR_ARG
+    assert frag in msg
+
+
+def test_null_handle_calls_fail_cleanly(clbm):
+    L = clbm.lib()
+    out = ctypes.c_double()
+    assert L.clbm_step(None, 1) == clbm.ERR_ARG
+    assert L.clbm_residual(None, ctypes.byref(out)) == clbm.ERR_ARG
+    assert L.clbm_destroy(None) == clbm.OK

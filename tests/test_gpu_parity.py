@@ -1,0 +1,213 @@
+"""GPU path against the FP64 CPU oracle, through the C ABI.
+
+Tolerances:
+  * FP64 storage and math: max|du|/U <= 1e-10 after 1000 steps (the bar of
+    the FP64 form); populations to 1e-12; one collision to 1e-14.
+  * FP32 storage and math: one collision to 1e-6 absolute (FP32 rounding of
+    the omega solve and of moments of size ~0.1); velocity L2 error <= 1e-4
+    relative over a run.
+  * FP16S storage (FP32 math): one collision within the FP16 half-ulp of the
+    stored output plus FP32 noise; velocity L2 error <= 2e-3 relative.
+The oracle is fed the same storage-rounded inputs where a single collision is
+compared, so those tolerances measure the arithmetic, not the input rounding.
+"""
+import numpy as np
+import pytest
+
+from paper_1908_05396_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def clbm():
+    from paper_1908_05396_gb300 import build
+    build.build()
+    from paper_1908_05396_gb300 import clbm as c
+    c.lib()
+    return c
+
+
+def _oracle_params(oracle, prob):
+    return oracle.Params(nx=prob.nx, ny=prob.ny, nz=prob.nz, face=prob.face, K=prob.K, n=prob.n,
+                         U=prob.U_lid, F=prob.body_force)
+
+
+def _lattice(clbm, prob, dtype, **kw):
+    return clbm.Lattice(**prob.kwargs(), dtype=dtype, **kw)
+
+
+def _round_dev(f, w, dtype):
+    """Populations as the storage holds them: f - w rounded, plus w."""
+    d = f - w[:, None]
+    if dtype == "f32":
+        d = d.astype(np.float32).astype(np.float64)
+    elif dtype == "f16s":
+        # the library rounds to FP32 first, then scales by 1024 (exact) and
+        # rounds to FP16, both to nearest even
+        d = (d.astype(np.float32) * np.float32(1024.0)).astype(np.float16).astype(np.float64) / 1024.0
+    return d + w[:, None]
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-14), ("f32", 1e-6), ("f16s", None)])
+@pytest.mark.parametrize("n,F", [(1.0, None), (0.5, None), (1.5, None),
+                                 (0.8, (2e-4, -1e-4, 5e-5))])
+def test_collide_nodes_vs_oracle(clbm, oracle, dtype, tol, n, F):
+    M = 3000
+    w = oracle.weights()
+    rng = np.random.default_rng(11)
+    # near-equilibrium states with velocities up to ~0.1 and strong
+    # non-equilibrium parts, plus a few exactly-at-rest nodes (zero shear)
+    f = w[:, None] * (1 + rng.uniform(-0.15, 0.15, (19, M))) * rng.uniform(0.9, 1.1, (1, M))
+    f[:, :5] = w[:, None]
+    K = 0.02
+    got = clbm.collide_nodes(f, K=K, n=n, dtype=dtype, body_force=F)
+    fin = _round_dev(f, w, dtype)
+    p = oracle.Params(K=K, n=n, F=F or (0, 0, 0))
+    ref = np.empty_like(f)
+    ref_u = np.empty((3, M))
+    ref_gd = np.empty(M)
+    for k in range(M):
+        r = oracle.collide(p, fin[:, k])
+        ref[:, k], ref_u[:, k], ref_gd[k] = r["ft"], r["u"], r["gamma_dot"]
+    if dtype == "f16s":
+        # output is rounded to FP16 after the collision: half an ulp of the
+        # stored deviation (2^-11 relative) plus FP32 arithmetic noise
+        dev = np.abs(ref - w[:, None])
+        bound = dev * 2.0 ** -11 + 2e-6
+        assert np.all(np.abs(got["ft"] - ref) <= bound)
+    else:
+        assert np.abs(got["ft"] - ref).max() <= tol
+    utol = 1e-15 if dtype == "f64" else 2e-6
+    assert np.abs(got["u"] - ref_u).max() <= utol
+    # relative agreement, with an absolute floor at the round-off of the O(1)
+    # moments that the shear rate is formed from
+    gtol, gfloor = (1e-12, 1e-14) if dtype == "f64" else (2e-4, 1e-7)
+    assert np.all(np.abs(got["gamma_dot"] - ref_gd) <= gtol * ref_gd + gfloor)
+
+
+def test_rest_states_agree(clbm, oracle):
+    prob = wl.cavity(8, 100.0, 1.0)
+    with _lattice(clbm, prob, "f64") as lat:
+        f = lat.get_state()
+    assert np.array_equal(f, oracle.rest_state(_oracle_params(oracle, prob)))
+
+
+@pytest.mark.parametrize("n", [0.5, 1.0, 1.5])
+def test_cavity_f64_1000_steps(clbm, oracle, n):
+    prob = wl.cavity(32, 100.0, n)
+    p = _oracle_params(oracle, prob)
+    with _lattice(clbm, prob, "f64") as lat:
+        lat.step(1000)
+        _, u_gpu, _ = lat.fields()
+        f_gpu = lat.get_state()
+    f_ref = oracle.run(p, oracle.rest_state(p), 1000)
+    _, u_ref, _ = oracle.fields(p, f_ref)
+    U = prob.U_lid[0]
+    assert np.abs(u_gpu - u_ref).max() / U <= 1e-10
+    assert np.abs(f_gpu - f_ref).max() <= 1e-12
+
+
+def test_channel_f64_1000_steps(clbm, oracle):
+    prob = wl.channel(64, 0.5, u_max=0.02, G=1e-6)
+    assert abs(prob.K - 7.3901e-4) < 1e-7
+    p = _oracle_params(oracle, prob)
+    with _lattice(clbm, prob, "f64") as lat:
+        lat.step(1000)
+        _, u_gpu, gd_gpu = lat.fields()
+    f_ref = oracle.run(p, oracle.rest_state(p), 1000)
+    _, u_ref, gd_ref = oracle.fields(p, f_ref)
+    assert np.abs(u_gpu - u_ref).max() / 0.02 <= 1e-10
+    assert np.abs(gd_gpu - gd_ref).max() <= 1e-10 * gd_ref.max()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s"])
+def test_ragged_mixed_boundaries_random_state(clbm, oracle, dtype):
+    # 33 x 17 x 9: ragged against every tile shape; walls on x, wall + lid on
+    # y, periodic z; a random perturbed initial state.
+    prob = wl.Problem("mixed", 33, 17, 9, (wl.WALL, wl.WALL, wl.WALL, wl.LID, wl.PERIODIC, wl.PERIODIC),
+                      K=0.01, n=0.7, U_lid=(0.04, 0.0, 0.02), body_force=(1e-5, 0.0, -2e-6))
+    p = _oracle_params(oracle, prob)
+    r = wl.noise((19, 9, 17, 33), seed=5, amp=0.05)
+    with _lattice(clbm, prob, dtype) as lat:
+        rest = lat.get_state()
+        f0 = rest * (1 + r)
+        lat.set_state(f0)
+        lat.step(200)
+        _, u_gpu, _ = lat.fields()
+    rest_o = oracle.rest_state(p)
+    assert np.array_equal(rest, rest_o)
+    f_ref = oracle.run(p, rest_o * (1 + r), 200)
+    _, u_ref, _ = oracle.fields(p, f_ref)
+    err = np.abs(u_gpu - u_ref).max() / 0.04
+    l2 = np.linalg.norm(u_gpu - u_ref) / np.linalg.norm(u_ref)
+    if dtype == "f64":
+        assert err <= 1e-10
+    elif dtype == "f32":
+        assert l2 <= 1e-4
+    else:
+        assert l2 <= 2e-3
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s"])
+def test_full_size_cavity_one_step(clbm, oracle, dtype):
+    # 128^3 cavity (the benchmark lattice, bench launch shape): one step from a
+    # random perturbed state, every node compared with the oracle.
+    prob = wl.cavity(128, 100.0, 0.5)
+    p = _oracle_params(oracle, prob)
+    r = wl.noise((19, 128, 128, 128), seed=3, amp=0.02)
+    with _lattice(clbm, prob, dtype) as lat:
+        rest = lat.get_state()
+        lat.set_state(rest * (1 + r))
+        lat.step(1)
+        f_gpu = lat.get_state()
+    w = oracle.weights()
+    f0 = oracle.rest_state(p) * (1 + r)
+    f0 = _round_dev(f0.reshape(19, -1), w, dtype).reshape(f0.shape)
+    f_ref = oracle.run(p, f0, 1)
+    dev = np.abs(f_ref - w[:, None, None, None])
+    if dtype == "f64":
+        assert np.abs(f_gpu - f_ref).max() <= 1e-14
+    elif dtype == "f32":
+        assert np.abs(f_gpu - f_ref).max() <= 1e-6
+    else:
+        assert np.all(np.abs(f_gpu - f_ref) <= dev * 2.0 ** -11 + 2e-6)
+
+
+def test_mass_conserved_and_residual_defined(clbm):
+    prob = wl.cavity(24, 100.0, 0.8)
+    with _lattice(clbm, prob, "f64", check_interval=50) as lat:
+        lat.step(49)
+        R, rc = lat.residual()
+        assert R == float("inf") and rc == 0
+        lat.step(1)
+        m = lat.mass()
+        assert abs(m - prob.N) <= 1e-12 * prob.N
+        lat.step(50)
+        R, rc = lat.residual()
+        assert 0 < R < 1 and rc == 0
+        lat.step(400)
+        assert abs(lat.mass() - prob.N) <= 1e-12 * prob.N
+
+
+def test_divergence_is_reported(clbm):
+    prob = wl.cavity(8, 100.0, 1.0)
+    with _lattice(clbm, prob, "f32", check_interval=10) as lat:
+        f = lat.get_state()
+        f[3, 4, 4, 4] = np.nan
+        lat.set_state(f)
+        lat.step(10)
+        _, rc = lat.residual()
+        assert rc == clbm.ERR_DIVERGED
+        lat.step(10)
+        assert lat.step(1) == clbm.ERR_DIVERGED
+
+
+def test_f64_bitwise_reproducible(clbm):
+    prob = wl.cavity(20, 400.0, 0.6)
+    outs = []
+    for _ in range(2):
+        with _lattice(clbm, prob, "f64") as lat:
+            lat.step(300)
+            outs.append(lat.get_state())
+    assert np.array_equal(outs[0], outs[1])
