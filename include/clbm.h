@@ -153,6 +153,44 @@ int clbm_collide_nodes(clbm_dtype dtype, double K, double n,
                        double nu_max, const double* f_in, double* f_out,
                        double* rho, double* u, double* gamma_dot, int64_t M);
 
+/* One check step between caller-owned device buffers, with no device memory
+ * allocated by the library.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc while they step -- a host
+ * application that hands out a fixed device-memory pool reserved at start-up,
+ * a framework that has already claimed the whole device, or code that must
+ * not stall on the allocator's implicit synchronisation.  It allocates
+ * nothing and calls no allocating library routine.
+ *
+ * It runs the same fused pull-stream + collide step as a check step of
+ * clbm_step() (Eqs. cascadedstreaming1, cascadedcollision1) from src to dst:
+ *   d, K, n, U_lid, body_force, dtype: as for clbm_create(); d->stream is the
+ *          CUDA stream to queue on (NULL: the legacy default stream);
+ *          d->check_interval is ignored.
+ *   src, dst: device buffers of 19 x N stored values in the dtype's storage
+ *          type (double, float, or FP16 bits), dense layout [q][z][y][x]
+ *          with no padding, holding f - w rho0 (times 1024 for F16S); src is
+ *          read, dst is written; they must not overlap.
+ *   u_prev: device buffer of 3 x N velocities [component][z][y][x] in the
+ *          math type (double for F64, float otherwise): read as the previous
+ *          check's velocity, overwritten with this step's.
+ *   stats:  device pointer to 4 doubles, written with sum |u - u_prev|^2,
+ *          sum |u|^2, sum (rho - rho0) and a divergence flag (0 or 1).
+ * The per-block partial sums of the reductions live in a fixed array of
+ * 65536 x 4 doubles (2 MiB) inside the library, which every GPU that loads
+ * the library holds until the process exits; a lattice needing more than
+ * 65536 blocks of 32 x 4 nodes (about 8.4 million nodes) is rejected with
+ * CLBM_ERR_ARG and a message from clbm_last_error(NULL).  Each call rewrites
+ * all the partial sums it reads, so no state carries over between calls, but
+ * calls that overlap on the GPU (on different streams, or on the same device
+ * from different threads) share that array and race.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.
+ * Queues two kernels and returns without synchronising.
+ * Errors: CLBM_ERR_ARG, CLBM_ERR_CUDA (text via clbm_last_error(NULL)). */
+int clbm_step_noalloc(const clbm_domain* d, double K, double n, const double U_lid[3],
+                      const double body_force[3], clbm_dtype dtype, const void* src,
+                      void* dst, void* u_prev, double* stats);
+
 #ifdef __cplusplus
 }
 #endif

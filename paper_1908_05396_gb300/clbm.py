@@ -212,3 +212,35 @@ def collide_nodes(f: np.ndarray, K: float, n: float, dtype="f64", body_force=Non
                                     float(nu_min), float(nu_max), _dp(f), _dp(out), _dp(rho),
                                     _dp(u), _dp(gd), M))
     return dict(ft=out, rho=rho, u=u, gamma_dot=gd)
+
+
+def step_noalloc(nx, ny, nz, face, K, n, U_lid, body_force, dtype, src, dst, u_prev, stats,
+                 rho0=1.0, nu_min=0.0, nu_max=0.0, stream=None) -> int:
+    """One check step between caller-owned device buffers (``clbm_step_noalloc``).
+
+    ``src``, ``dst``, ``u_prev`` and ``stats`` are device addresses (ints) of
+    buffers the caller owns, in the dense layouts the header documents.
+    Returns the status code; the message of a failure is in
+    ``last_error()``."""
+    L = lib()
+    if not hasattr(L, "_noalloc_ready"):
+        L.clbm_step_noalloc.argtypes = [ctypes.POINTER(Domain), ctypes.c_double, ctypes.c_double,
+                                        _D, _D, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]
+        L.clbm_step_noalloc.restype = ctypes.c_int
+        L._noalloc_ready = True
+    d = Domain()
+    d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
+    for i, f in enumerate(face):
+        d.face[i] = int(f)
+    d.rho0, d.nu_min, d.nu_max = float(rho0), float(nu_min), float(nu_max)
+    d.stream = stream
+    code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    return L.clbm_step_noalloc(ctypes.byref(d), float(K), float(n), _vec3(U_lid), _vec3(body_force),
+                               code, ctypes.c_void_p(src), ctypes.c_void_p(dst),
+                               ctypes.c_void_p(u_prev), ctypes.c_void_p(stats))
+
+
+def last_error() -> str:
+    msg = lib().clbm_last_error(None)
+    return msg.decode() if msg else ""

@@ -110,6 +110,10 @@ int check_phys(double K, double n, double nu_min, double nu_max, std::string& wh
 
 }  // namespace
 
+namespace clbm {
+void set_unbound_error(const char* msg) { g_create_err = msg; }
+}  // namespace clbm
+
 extern "C" {
 
 int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],

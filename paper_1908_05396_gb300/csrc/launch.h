@@ -58,6 +58,9 @@ struct CheckBufs {
   cudaError_t launch_import_##SUFFIX(const double* in, const Geom& g, double rho0,            \
                                      double inv_scale, void* dst, cudaStream_t st);
 
+// Record the text that clbm_last_error(NULL) returns on this thread.
+void set_unbound_error(const char* msg);
+
 CLBM_DECLARE_LAUNCHERS(f64)
 CLBM_DECLARE_LAUNCHERS(f32)
 CLBM_DECLARE_LAUNCHERS(f16)
