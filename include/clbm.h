@@ -137,6 +137,24 @@ int clbm_sync(clbm_handle h);
 /* Free the handle and its device memory.  NULL is accepted. */
 int clbm_destroy(clbm_handle h);
 
+/* Pick the launch shape of h's step kernel by timing: thread-block shapes
+ * from 32x1 to 256x1 and, for the FP32-math forms, one or two nodes per
+ * thread (two nodes are collided together with packed FP32 instructions).
+ * Each candidate runs `steps` steps (<= 0 -> 10) after two warm-up steps,
+ * timed with CUDA events on the handle's stream; the state is saved first
+ * and restored afterwards, and the step counter does not move.  The choice
+ * is cached per (dtype, nx, ny, nz, force, Newtonian) for the process, so
+ * later handles of the same kind reuse it without timing.  Any output
+ * pointer may be NULL.  Synchronises; temporarily needs one extra population
+ * buffer of device memory. */
+int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt,
+                  double* us_per_step);
+
+/* Set the launch shape of h's step kernel directly: block_x * block_y
+ * threads (a multiple of 32, at most 256; at most 128 when npt = 2) and
+ * npt = 1 or 2 nodes per thread (2 only for the FP32 and F16S forms). */
+int clbm_set_launch(clbm_handle h, int block_x, int block_y, int npt);
+
 /* Text of the last error on h (never NULL); h may be NULL for errors of
  * clbm_create. */
 const char* clbm_last_error(clbm_handle h);

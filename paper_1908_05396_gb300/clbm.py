@@ -71,7 +71,12 @@ def lib():
             L.clbm_collide_nodes.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _D,
                                              ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                              _D, _D, _D, _D, _D, ctypes.c_int64]
-            for name in ("clbm_create", "clbm_step", "clbm_fields", "clbm_fields_device",
+            L.clbm_autotune.argtypes = [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        _D]
+            L.clbm_set_launch.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            for name in ("clbm_autotune", "clbm_set_launch",
+                         "clbm_create", "clbm_step", "clbm_fields", "clbm_fields_device",
                          "clbm_residual", "clbm_mass", "clbm_get_state", "clbm_set_state",
                          "clbm_steps_done", "clbm_sync", "clbm_destroy", "clbm_collide_nodes"):
                 getattr(L, name).restype = ctypes.c_int
@@ -171,6 +176,17 @@ class Lattice:
         f = np.ascontiguousarray(f, dtype=np.float64)
         assert f.shape == (19,) + self.shape
         _check(lib().clbm_set_state(self._h, _dp(f)), self._h)
+
+    def autotune(self, steps: int = 10) -> dict:
+        """Time the launch-shape candidates and keep the fastest (state restored)."""
+        bx, by, npt = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        us = ctypes.c_double()
+        _check(lib().clbm_autotune(self._h, int(steps), ctypes.byref(bx), ctypes.byref(by),
+                                   ctypes.byref(npt), ctypes.byref(us)), self._h)
+        return dict(block=(bx.value, by.value), npt=npt.value, us_per_step=us.value)
+
+    def set_launch(self, block_x: int, block_y: int, npt: int) -> None:
+        _check(lib().clbm_set_launch(self._h, int(block_x), int(block_y), int(npt)), self._h)
 
     def steps_done(self) -> int:
         out = ctypes.c_int64(0)

@@ -9,8 +9,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
+#include <vector>
 
 #include "../../include/clbm.h"
 #include "launch.h"
@@ -38,6 +42,7 @@ struct clbm_ctx {
   int64_t checks = 0;    // check steps queued so far
   bool diverged = false; // sticky once a completed check saw divergence
   dim3 block{32, 4, 1};
+  int npt = 1;           // nodes per thread (1 or 2), + 4 for the register-capped kernel
   std::string err;
 };
 
@@ -69,9 +74,9 @@ cudaError_t dispatch_step(clbm_ctx* h, bool check) {
   const void* src = h->buf[h->cur];
   void* dst = h->buf[1 - h->cur];
   switch (h->dtype) {
-    case CLBM_F64: return launch_step_f64(src, dst, h->g, h->P, cb, check, h->block, h->stream);
-    case CLBM_F32: return launch_step_f32(src, dst, h->g, h->P, cb, check, h->block, h->stream);
-    default: return launch_step_f16(src, dst, h->g, h->P, cb, check, h->block, h->stream);
+    case CLBM_F64: return launch_step_f64(src, dst, h->g, h->P, cb, check, h->block, 1, h->stream);
+    case CLBM_F32: return launch_step_f32(src, dst, h->g, h->P, cb, check, h->block, h->npt, h->stream);
+    default: return launch_step_f16(src, dst, h->g, h->P, cb, check, h->block, h->npt, h->stream);
   }
 }
 
@@ -186,6 +191,7 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
   h->block.x = d->nx <= 32 ? 32 : d->nx <= 64 ? 64 : 128;
   h->block.y = 128 / h->block.x;
   h->block.z = 1;
+  h->npt = dtype == CLBM_F64 ? 1 : 2;
 
   auto cleanup = [&](int code, const std::string& m) {
     g_create_err = m + (h->err.empty() ? "" : (": " + h->err));
@@ -375,6 +381,125 @@ int clbm_sync(clbm_handle h) {
   if (bad(h)) return fail(h, CLBM_ERR_ARG, "invalid handle");
   if (int r = set_device(h)) return r;
   CK(h, cudaStreamSynchronize(h->stream));
+  return CLBM_OK;
+}
+
+namespace {
+// Autotuner cache: (dtype, nx, ny, nz, force, newtonian) -> (bx, by, npt).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int>, std::tuple<int, int, int, double>> g_tune;
+}  // namespace
+
+int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt,
+                  double* us_per_step) {
+  if (bad(h)) return fail(h, CLBM_ERR_ARG, "invalid handle");
+  if (int r = set_device(h)) return r;
+  if (steps <= 0) steps = 10;
+  const auto key = std::make_tuple(int(h->dtype), h->g.nx, h->g.ny, h->g.nz, h->P.has_force,
+                                   h->P.newtonian);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      h->block = dim3(std::get<0>(it->second), std::get<1>(it->second), 1);
+      h->npt = std::get<2>(it->second);
+      if (block_x) *block_x = h->block.x;
+      if (block_y) *block_y = h->block.y;
+      if (npt) *npt = h->npt;
+      if (us_per_step) *us_per_step = std::get<3>(it->second);
+      return CLBM_OK;
+    }
+  }
+  // Candidates: block shapes up to 256 threads (128 for two nodes per thread,
+  // whose kernel is compiled for 128), x extent at most the padded row.
+  struct Cand { int bx, by, npt; };
+  std::vector<Cand> cands;
+  const int shapes[][2] = {{32, 1}, {32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2}, {64, 4},
+                           {128, 1}, {128, 2}, {256, 1}};
+  for (int capped = 0; capped <= 1; ++capped)
+    for (int np = 1; np <= (h->dtype == CLBM_F64 ? 1 : 2); ++np)
+      for (auto& sh : shapes) {
+        if (sh[0] * sh[1] > (np == 2 ? 128 : 256)) continue;
+        if (sh[0] > 32 && sh[0] > h->g.pitch) continue;
+        cands.push_back({sh[0], sh[1], np + 4 * capped});
+      }
+  // Save the state: tuning runs real steps.
+  const size_t pop_bytes = size_t(NQ) * size_t(h->g.qstride) * h->elem;
+  void* saved = nullptr;
+  CK(h, cudaMallocAsync(&saved, pop_bytes, h->stream));
+  CK(h, cudaMemcpyAsync(saved, h->buf[h->cur], pop_bytes, cudaMemcpyDeviceToDevice, h->stream));
+  const int cur0 = h->cur;
+  cudaEvent_t e0, e1;
+  CK(h, cudaEventCreate(&e0));
+  CK(h, cudaEventCreate(&e1));
+  const dim3 block0 = h->block;
+  const int npt0 = h->npt;
+  double best = 1e300;
+  Cand bestc{int(block0.x), int(block0.y), npt0};
+  cudaError_t err = cudaSuccess;
+  for (const Cand& c : cands) {
+    h->block = dim3(c.bx, c.by, 1);
+    h->npt = c.npt;
+    for (int s = 0; s < 2 && err == cudaSuccess; ++s) {
+      err = dispatch_step(h, false);
+      h->cur = 1 - h->cur;
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(e0, h->stream);
+    for (int s = 0; s < steps && err == cudaSuccess; ++s) {
+      err = dispatch_step(h, false);
+      h->cur = 1 - h->cur;
+    }
+    if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err != cudaSuccess) break;
+    const double us = 1e3 * double(ms) / steps;
+    if (us < best) {
+      best = us;
+      bestc = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // Restore the state into the buffer that held it.
+  h->cur = cur0;
+  cudaError_t e2 = cudaMemcpyAsync(h->buf[h->cur], saved, pop_bytes, cudaMemcpyDeviceToDevice,
+                                   h->stream);
+  cudaFreeAsync(saved, h->stream);
+  if (err == cudaSuccess) err = e2;
+  if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+  if (err != cudaSuccess) {
+    h->block = block0;
+    h->npt = npt0;
+    return cuda_fail(h, err, "clbm_autotune");
+  }
+  h->block = dim3(bestc.bx, bestc.by, 1);
+  h->npt = bestc.npt;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = std::make_tuple(bestc.bx, bestc.by, bestc.npt, best);
+  }
+  if (block_x) *block_x = bestc.bx;
+  if (block_y) *block_y = bestc.by;
+  if (npt) *npt = bestc.npt;
+  if (us_per_step) *us_per_step = best;
+  return CLBM_OK;
+}
+
+int clbm_set_launch(clbm_handle h, int block_x, int block_y, int npt) {
+  if (bad(h)) return fail(h, CLBM_ERR_ARG, "invalid handle");
+  const int np = npt & 3;
+  if ((np != 1 && np != 2) || (npt & ~7))
+    return fail(h, CLBM_ERR_ARG, "npt must be 1 or 2, plus 4 for the register-capped kernel");
+  if (block_x < 1 || block_y < 1 || block_x * block_y > (np == 2 ? 128 : 256) ||
+      block_x * block_y % 32 != 0)
+    return fail(h, CLBM_ERR_ARG, "block must have a multiple of 32 threads, at most 256 "
+                                 "(128 with two nodes per thread)");
+  if (np == 2 && h->dtype == CLBM_F64)
+    return fail(h, CLBM_ERR_UNSUPPORTED, "two nodes per thread needs FP32 math");
+  h->block = dim3(block_x, block_y, 1);
+  h->npt = npt;
   return CLBM_OK;
 }
 

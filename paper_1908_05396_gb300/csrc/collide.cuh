@@ -11,8 +11,14 @@
 #pragma once
 
 #include "d3q19.cuh"
+#include "v2.cuh"
 
 namespace clbm {
+
+// Scalar type of the per-lattice constants for a math type R (a pair of FP32
+// nodes uses FP32 constants).
+template <typename R> struct ScalarOf { using type = R; };
+template <> struct ScalarOf<V2> { using type = float; };
 
 // Per-lattice constants of the collision, in the math precision R.
 template <typename R>
@@ -45,9 +51,24 @@ template <typename R> __device__ __forceinline__ R rdiv(R a, R b);
 template <> __device__ __forceinline__ float rdiv<float>(float a, float b) { return __fdividef(a, b); }
 template <> __device__ __forceinline__ double rdiv<double>(double a, double b) { return a / b; }
 
+// Reciprocal: fast approximate (MUFU based, ~1 ulp) in FP32, IEEE in FP64.
+template <typename R> __device__ __forceinline__ R rrcp(R x);
+template <> __device__ __forceinline__ float rrcp<float>(float x) { return __fdividef(1.0f, x); }
+template <> __device__ __forceinline__ double rrcp<double>(double x) { return 1.0 / x; }
+
+template <> __device__ __forceinline__ V2 rlog<V2>(V2 x) { return V2(__logf(x.v.x), __logf(x.v.y)); }
+template <> __device__ __forceinline__ V2 rexp<V2>(V2 x) { return V2(__expf(x.v.x), __expf(x.v.y)); }
+template <> __device__ __forceinline__ V2 rdiv<V2>(V2 a, V2 b) {
+  return V2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y));
+}
+template <> __device__ __forceinline__ V2 rrcp<V2>(V2 x) {
+  return V2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y));
+}
+
 template <typename R> __device__ __forceinline__ R tiny();
 template <> __device__ __forceinline__ float tiny<float>() { return 1e-36f; }
 template <> __device__ __forceinline__ double tiny<double>() { return 1e-300; }
+template <> __device__ __forceinline__ V2 tiny<V2>() { return V2(1e-36f); }
 
 // Newton iterations on y = log(1/omega - 1/2) for
 //   G(y) = y - log(3K/rho) - (n-1)/2 log(omega(y)^2 A + B) = 0,
@@ -65,7 +86,7 @@ __device__ __forceinline__ R newton_y(R y, R c, R ehalf, R nm1, R A, R B,
 #pragma unroll 1
   for (int it = 0; it < iters; ++it) {
     R tau = rexp<R>(y);
-    R w = R(1) / (tau + R(0.5));
+    R w = rrcp<R>(tau + R(0.5));
     R wwA = w * w * A;
     R g2 = fmax(wwA + B, tiny<R>());
     R G = y - c - ehalf * rlog<R>(g2);
@@ -76,39 +97,55 @@ __device__ __forceinline__ R newton_y(R y, R c, R ehalf, R nm1, R A, R B,
 }
 
 // omega_nu from A and B (see above); writes |gamma_dot| at that omega.
+// FP32 (one node or a pair): four Newton iterations from the guess
+// omega = 2/3 reach the FP32 rounding level.
 template <typename R>
-__device__ __forceinline__ R omega_nu(const CollideConst<R>& C, R rho, R A,
-                                      R B, R* gd) {
+__device__ __forceinline__ R omega_nu(const CollideConst<float>& C, R rho, R rinv, R A, R B,
+                                      R* gd) {
   R w;
   if (C.newtonian) {
-    R nu = fmin(fmax(C.K3 / (R(3) * rho), C.nu_min), C.nu_max);
-    w = R(1) / (R(3) * nu + R(0.5));
+    R nu = fmin(fmax(R(C.K3 * (1.0f / 3.0f)) * rinv, R(C.nu_min)), R(C.nu_max));
+    w = rrcp<R>(R(3.0f) * nu + R(0.5f));
   } else {
-    // Four single-precision iterations from the guess omega = 2/3 reach the
-    // FP32 rounding level; the FP64 form polishes with two more in FP64.
+    const R c = R(C.logK3) - rlog<R>(rho);
+    R y0 = c + R(C.ehalf) * rlog<R>(fmax(A * R(4.0f / 9.0f) + B, tiny<R>()));
+    y0 = fmin(fmax(y0, R(C.ylo)), R(C.yhi));
+    const R y = newton_y<R>(y0, c, R(C.ehalf), R(C.n - 1.0f), A, B, R(C.ylo), R(C.yhi), 4);
+    w = rrcp<R>(rexp<R>(y) + R(0.5f));
+  }
+  *gd = sqrt(fmax(w * w * A + B, R(0.0f)));
+  return w;
+}
+
+// FP64: the same four iterations in FP32, then two in FP64, which take the
+// FP32 estimate to the FP64 rounding level (quadratic convergence).
+__device__ __forceinline__ double omega_nu(const CollideConst<double>& C, double rho,
+                                           double rinv, double A, double B, double* gd) {
+  double w;
+  if (C.newtonian) {
+    double nu = fmin(fmax(C.K3 * (1.0 / 3.0) * rinv, C.nu_min), C.nu_max);
+    w = 1.0 / (3.0 * nu + 0.5);
+  } else {
     float cf = float(C.logK3) - __logf(float(rho));
     float Af = float(A), Bf = float(B);
-    float y0 = cf + float(C.ehalf) *
-                        __logf(fmaxf(Af * (4.0f / 9.0f) + Bf, 1e-36f));
+    float y0 = cf + float(C.ehalf) * __logf(fmaxf(Af * (4.0f / 9.0f) + Bf, 1e-36f));
     y0 = fminf(fmaxf(y0, float(C.ylo)), float(C.yhi));
-    float yf = newton_y<float>(y0, cf, float(C.ehalf), float(C.n) - 1.0f, Af,
-                               Bf, float(C.ylo), float(C.yhi), 4);
-    R y = R(yf);
-    if (sizeof(R) == 8) {
-      R c = C.logK3 - rlog<R>(rho);
-      y = newton_y<R>(y, c, C.ehalf, C.n - R(1), A, B, C.ylo, C.yhi, 2);
-    }
-    w = R(1) / (rexp<R>(y) + R(0.5));
+    float yf = newton_y<float>(y0, cf, float(C.ehalf), float(C.n) - 1.0f, Af, Bf,
+                               float(C.ylo), float(C.yhi), 4);
+    const double c = C.logK3 - log(rho);
+    double y = newton_y<double>(double(yf), c, C.ehalf, C.n - 1.0, A, B, C.ylo, C.yhi, 2);
+    w = 1.0 / (exp(y) + 0.5);
   }
-  *gd = sqrt(fmax(w * w * A + B, R(0)));
+  *gd = sqrt(fmax(w * w * A + B, 0.0));
   return w;
 }
 
 // Collide one node.  d[19] holds the pre-collision deviations on entry and
 // the post-collision deviations f~ - w rho0 on return.
 template <typename R, bool FORCE>
-__device__ __forceinline__ void collide(const CollideConst<R>& C, R (&d)[Q],
-                                        NodeOut<R>& out) {
+__device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>::type>& C,
+                                        R (&d)[Q], NodeOut<R>& out) {
+  using T = typename ScalarOf<R>::type;
   // ---- mass and momentum (Eqs. hydrodynamicfields1/2) -------------------
   R s[NPAIR], t[NPAIR];
 #pragma unroll
@@ -126,16 +163,16 @@ __device__ __forceinline__ void collide(const CollideConst<R>& C, R (&d)[Q],
     if (cy(q)) jy += R(cy(q)) * t[p];
     if (cz(q)) jz += R(cz(q)) * t[p];
   }
-  const R rho = C.rho0 + drho;
-  const R rinv = R(1) / rho;
+  const R rho = R(C.rho0) + drho;
+  const R rinv = rrcp<R>(rho);
   R ux, uy, uz;
   if (FORCE) {
     // Symmetric split of the body force: the velocity is (j + F/2)/rho and
     // half of the source S_a = w_a [3 e.F + 9 (e.u)(e.F) - 3 u.F] is added
     // before the collision (its moments are 0, F and uF + Fu).
-    ux = (jx + R(0.5) * C.F[0]) * rinv;
-    uy = (jy + R(0.5) * C.F[1]) * rinv;
-    uz = (jz + R(0.5) * C.F[2]) * rinv;
+    ux = (jx + R(T(0.5) * C.F[0])) * rinv;
+    uy = (jy + R(T(0.5) * C.F[1])) * rinv;
+    uz = (jz + R(T(0.5) * C.F[2])) * rinv;
   } else {
     ux = jx * rinv;
     uy = jy * rinv;
@@ -143,12 +180,12 @@ __device__ __forceinline__ void collide(const CollideConst<R>& C, R (&d)[Q],
   }
   R Sa[FORCE ? Q : 1];
   if (FORCE) {
-    const R uF = ux * C.F[0] + uy * C.F[1] + uz * C.F[2];
+    const R uF = ux * R(C.F[0]) + uy * R(C.F[1]) + uz * R(C.F[2]);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      R eF = R(cx(q)) * C.F[0] + R(cy(q)) * C.F[1] + R(cz(q)) * C.F[2];
+      const T eF = T(cx(q)) * C.F[0] + T(cy(q)) * C.F[1] + T(cz(q)) * C.F[2];
       R eu = R(cx(q)) * ux + R(cy(q)) * uy + R(cz(q)) * uz;
-      Sa[q] = wt<R>(q) * (R(3) * eF + R(9) * eu * eF - R(3) * uF);
+      Sa[q] = R(wt<T>(q)) * (R(T(3) * eF) + R(T(9) * eF) * eu - R(3) * uF);
       d[q] += R(0.5) * Sa[q];
     }
 #pragma unroll
@@ -185,7 +222,7 @@ __device__ __forceinline__ void collide(const CollideConst<R>& C, R (&d)[Q],
   }
 
   const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-  const R r3 = C.rho0 * R(1.0 / 3.0);
+  const R r3 = R(C.rho0 * T(1.0 / 3.0));
   const R kxx = r3 + Dxx, kyy = r3 + Dyy, kzz = r3 + Dzz;
 
   // ---- non-equilibrium second moments m^(1)_4..9 (Sec. 3.2) -------------
@@ -203,7 +240,7 @@ __device__ __forceinline__ void collide(const CollideConst<R>& C, R (&d)[Q],
   const R A = R(12) * q2 * (m7 * m7 - m7 * m8 + m8 * m8 + R(3) * (m4 * m4 + m5 * m5 + m6 * m6));
   const R B = R(6) * q2 * m9 * m9;
   R gd;
-  const R w = omega_nu<R>(C, rho, A, B, &gd);
+  const R w = omega_nu(C, rho, rinv, A, B, &gd);
 
   // ---- change of moments, Eqs. collisionkernelg4..g18 --------------------
   // omega_4..8 = w, omega_9..18 = 1 (Sec. 3.1).

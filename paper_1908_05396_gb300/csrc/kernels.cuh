@@ -13,6 +13,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "collide.cuh"
 #include "launch.h"
 
@@ -41,7 +43,7 @@ template <typename R> struct Codec<__half, R> {
 };
 
 template <typename R>
-__device__ __forceinline__ CollideConst<R> make_const(const PhysParams& P) {
+__host__ __device__ __forceinline__ CollideConst<R> make_const(const PhysParams& P) {
   CollideConst<R> C;
   C.rho0 = R(P.rho0);
   C.F[0] = R(P.F[0]);
@@ -125,33 +127,115 @@ __device__ __forceinline__ void block_sum_add(double v, double* acc, double* sme
   __syncthreads();
 }
 
-// One time step.  CHECK = true also writes u into uprev (after reading the
-// previous check's value there) and reduces sum|u - uprev|^2, sum|u|^2,
+// ---- the fused step ---------------------------------------------------------
+// Direction tables for the general pull, where the direction is a run-time value.
+static __constant__ signed char c_ex[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+static __constant__ signed char c_ey[Q] = {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1};
+static __constant__ signed char c_ez[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1};
+static __constant__ signed char c_opp[Q] = {0, 2, 1, 4, 3, 6, 5, 10, 9, 8, 7, 14, 13, 12, 11, 18, 17, 16, 15};
+
+// Everything one step launch needs, precomputed on the host in the math
+// precision R (no double arithmetic is left in the FP32 kernels).
+template <typename S, typename R>
+struct StepArgs {
+  const S* srcq[Q];  // srcq[q][i]: stored f~_q of the upwind neighbour of node i
+  S* dstq[Q];        // dstq[q][i]: slot of direction q of node i
+  const S* src;      // source buffer base (bounce-back and general path)
+  int64_t qstride;
+  int nx, ny, nz, pitch, plane;
+  unsigned facebits;
+  R lidc[Q];         // 6 w_q rho0 (e_q . U_lid): lid momentum correction
+  CollideConst<R> C;
+  CheckBufs cb;
+};
+
+// Pull of direction q into node (x, y, z) for nodes on a y or z face, where
+// any of the three source coordinates may leave the box.  Not inlined: it
+// runs only in warps on those faces, and one shared copy keeps the step
+// kernel small enough for the instruction cache.
+template <typename S, typename R>
+__device__ __noinline__ R pull_general(const S* __restrict__ src, int64_t qstride, int nx,
+                                       int ny, int nz, int pitch, int plane, unsigned facebits,
+                                       int q, int x, int y, int z, int i, R lid) {
+  int s0 = x - c_ex[q], s1 = y - c_ey[q], s2 = z - c_ez[q];
+  bool bounce = false, islid = false;
+  if (s0 < 0 || s0 >= nx) {
+    const int k = (facebits >> (s0 < 0 ? 0 : 2)) & 3;
+    if (k == BC_PERIODIC) s0 += s0 < 0 ? nx : -nx;
+    else { bounce = true; islid = k == BC_LID; }
+  }
+  if (s1 < 0 || s1 >= ny) {
+    const int k = (facebits >> (s1 < 0 ? 4 : 6)) & 3;
+    if (k == BC_PERIODIC) s1 += s1 < 0 ? ny : -ny;
+    else { bounce = true; islid = islid || k == BC_LID; }
+  }
+  if (s2 < 0 || s2 >= nz) {
+    const int k = (facebits >> (s2 < 0 ? 8 : 10)) & 3;
+    if (k == BC_PERIODIC) s2 += s2 < 0 ? nz : -nz;
+    else { bounce = true; islid = islid || k == BC_LID; }
+  }
+  if (bounce) {
+    R v = Codec<S, R>::dec(src[int64_t(c_opp[q]) * qstride + i], R(1));
+    return islid ? v + lid : v;
+  }
+  return Codec<S, R>::dec(src[int64_t(q) * qstride + s2 * plane + s1 * pitch + s0], R(1));
+}
+
+// One time step.  Warps off the y and z faces load all 19 upwind values
+// unconditionally and then, in the one or two lanes on an x face, replace the
+// five directions that come from outside the box; warps on a y or z face go
+// through pull_general.  CHECK = true also writes u into uprev (after reading
+// the previous check's value there) and reduces sum|u - uprev|^2, sum|u|^2,
 // sum(rho - rho0) and a divergence flag in FP64.
-template <typename S, typename R, bool FORCE, bool CHECK>
-__global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ src,
-                                                   S* __restrict__ dst, Geom g,
-                                                   PhysParams P, CheckBufs cb) {
+// CAP = true caps registers so that four 256-thread (or eight 128-thread)
+// blocks fit on an SM: more warps to hide DRAM latency, at the risk of
+// spills; the autotuner decides.
+template <typename S, typename R, bool FORCE, bool CHECK, bool CAP>
+__global__ void __launch_bounds__(256, CAP ? 4 : 1) step_kernel(const StepArgs<S, R> a) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
-  const bool active = x < g.nx && y < g.ny;
+  const bool active = x < a.nx && y < a.ny;
   if (!CHECK && !active) return;
-  const R inv_scale = R(P.inv_scale);
-  const CollideConst<R> C = make_const<R>(P);
   double du2 = 0.0, uu = 0.0, dr = 0.0;
   int bad = 0;
   if (active) {
-    const int64_t i = int64_t(z) * g.plane + int64_t(y) * g.pitch + x;
+    const int i = z * a.plane + y * a.pitch + x;
     R d[Q];
-    pull<S, R>(src, g, x, y, z, i, inv_scale, d);
-    NodeOut<R> o;
-    collide<R, FORCE>(C, d, o);
+    if (y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) dst[q * g.qstride + i] = Codec<S, R>::enc(d[q], inv_scale);
+      for (int q = 0; q < Q; ++q) d[q] = Codec<S, R>::dec(a.srcq[q][i], R(1));
+      if (x == 0 || x == a.nx - 1) {
+        const int kl = a.facebits & 3, kr = (a.facebits >> 2) & 3;
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+          if (cx(q) == 1 && x == 0) {
+            d[q] = kl == BC_PERIODIC
+                       ? Codec<S, R>::dec(a.srcq[q][i + a.nx], R(1))
+                       : Codec<S, R>::dec(a.src[opp(q) * a.qstride + i], R(1)) +
+                             (kl == BC_LID ? a.lidc[q] : R(0));
+          }
+          if (cx(q) == -1 && x == a.nx - 1) {
+            d[q] = kr == BC_PERIODIC
+                       ? Codec<S, R>::dec(a.srcq[q][i - a.nx], R(1))
+                       : Codec<S, R>::dec(a.src[opp(q) * a.qstride + i], R(1)) +
+                             (kr == BC_LID ? a.lidc[q] : R(0));
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        d[q] = pull_general<S, R>(a.src, a.qstride, a.nx, a.ny, a.nz, a.pitch, a.plane,
+                                  a.facebits, q, x, y, z, i, a.lidc[q]);
+    }
+    NodeOut<R> o;
+    collide<R, FORCE>(a.C, d, o);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) a.dstq[q][i] = Codec<S, R>::enc(d[q], R(1));
     if (CHECK) {
-      R* up = reinterpret_cast<R*>(cb.uprev);
-      const int64_t nst = g.plane * g.nz;
+      R* up = reinterpret_cast<R*>(a.cb.uprev);
+      const int64_t nst = int64_t(a.plane) * a.nz;
       const R px = up[i], py = up[nst + i], pz = up[2 * nst + i];
       up[i] = o.ux;
       up[nst + i] = o.uy;
@@ -161,17 +245,114 @@ __global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ src,
       du2 = ex * ex + ey * ey + ez * ez;
       uu = double(o.ux) * double(o.ux) + double(o.uy) * double(o.uy) +
            double(o.uz) * double(o.uz);
-      dr = double(o.rho) - double(P.rho0);
+      dr = double(o.rho) - double(a.C.rho0);
       const double chk = double(o.rho) + double(o.ux) + double(o.uy) + double(o.uz);
       bad = !(chk == chk) || !(fabs(chk) < 1e30) || !(double(o.rho) > 0.5 && double(o.rho) < 2.0);
     }
   }
   if (CHECK) {
     __shared__ double smem[32];
-    block_sum_add(du2, &cb.acc[0], smem);
-    block_sum_add(uu, &cb.acc[1], smem);
-    block_sum_add(dr, &cb.acc[2], smem);
-    if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(cb.flag, 1);
+    block_sum_add(du2, &a.cb.acc[0], smem);
+    block_sum_add(uu, &a.cb.acc[1], smem);
+    block_sum_add(dr, &a.cb.acc[2], smem);
+    if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(a.cb.flag, 1);
+  }
+}
+
+// Two nodes per thread, rows y and y + 1 at the same (x, z), collided as a
+// pair with packed FP32 arithmetic (R = V2).  Loads and stores stay 32-bit
+// per row, so every warp access still covers 32 consecutive x.  Both nodes
+// share x, so the x-face replacement is the same for the pair; a pair that
+// touches a y or z face pulls node by node through pull_general.
+template <typename S, bool FORCE, bool CHECK, bool CAP>
+__global__ void __launch_bounds__(128, CAP ? 4 : 1) step2_kernel(const StepArgs<S, float> a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = 2 * (blockIdx.y * blockDim.y + threadIdx.y);
+  const int z = blockIdx.z;
+  const bool activeA = x < a.nx && y < a.ny;
+  const bool activeB = activeA && y + 1 < a.ny;
+  if (!CHECK && !activeA) return;
+  double du2 = 0.0, uu = 0.0, dr = 0.0;
+  int bad = 0;
+  if (activeA) {
+    const int iA = z * a.plane + y * a.pitch + x;
+    const int iB = activeB ? iA + a.pitch : iA;
+    V2 d[Q];
+    if (y > 0 && y + 1 < a.ny - 1 && z > 0 && z < a.nz - 1) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        d[q] = V2(Codec<S, float>::dec(a.srcq[q][iA], 1.0f),
+                  Codec<S, float>::dec(a.srcq[q][iB], 1.0f));
+      if (x == 0 || x == a.nx - 1) {
+        const int kl = a.facebits & 3, kr = (a.facebits >> 2) & 3;
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+          if (cx(q) == 1 && x == 0) {
+            d[q] = kl == BC_PERIODIC
+                       ? V2(Codec<S, float>::dec(a.srcq[q][iA + a.nx], 1.0f),
+                            Codec<S, float>::dec(a.srcq[q][iB + a.nx], 1.0f))
+                       : V2(Codec<S, float>::dec(a.src[opp(q) * a.qstride + iA], 1.0f),
+                            Codec<S, float>::dec(a.src[opp(q) * a.qstride + iB], 1.0f)) +
+                             V2(kl == BC_LID ? a.lidc[q] : 0.0f);
+          }
+          if (cx(q) == -1 && x == a.nx - 1) {
+            d[q] = kr == BC_PERIODIC
+                       ? V2(Codec<S, float>::dec(a.srcq[q][iA - a.nx], 1.0f),
+                            Codec<S, float>::dec(a.srcq[q][iB - a.nx], 1.0f))
+                       : V2(Codec<S, float>::dec(a.src[opp(q) * a.qstride + iA], 1.0f),
+                            Codec<S, float>::dec(a.src[opp(q) * a.qstride + iB], 1.0f)) +
+                             V2(kr == BC_LID ? a.lidc[q] : 0.0f);
+          }
+        }
+      }
+    } else {
+      const int yB = activeB ? y + 1 : y;
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        d[q] = V2(pull_general<S, float>(a.src, a.qstride, a.nx, a.ny, a.nz, a.pitch, a.plane,
+                                         a.facebits, q, x, y, z, iA, a.lidc[q]),
+                  pull_general<S, float>(a.src, a.qstride, a.nx, a.ny, a.nz, a.pitch, a.plane,
+                                         a.facebits, q, x, yB, z, iB, a.lidc[q]));
+    }
+    NodeOut<V2> o;
+    collide<V2, FORCE>(a.C, d, o);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) a.dstq[q][iA] = Codec<S, float>::enc(lane0(d[q]), 1.0f);
+    if (activeB) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) a.dstq[q][iB] = Codec<S, float>::enc(lane1(d[q]), 1.0f);
+    }
+    if (CHECK) {
+      float* up = reinterpret_cast<float*>(a.cb.uprev);
+      const int64_t nst = int64_t(a.plane) * a.nz;
+      const float ux[2] = {lane0(o.ux), lane1(o.ux)}, uy[2] = {lane0(o.uy), lane1(o.uy)},
+                  uz[2] = {lane0(o.uz), lane1(o.uz)}, rh[2] = {lane0(o.rho), lane1(o.rho)};
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (k == 1 && !activeB) break;
+        const int i = k == 0 ? iA : iB;
+        const float px = up[i], py = up[nst + i], pz = up[2 * nst + i];
+        up[i] = ux[k];
+        up[nst + i] = uy[k];
+        up[2 * nst + i] = uz[k];
+        const double ex = double(ux[k]) - double(px), ey = double(uy[k]) - double(py),
+                     ez = double(uz[k]) - double(pz);
+        du2 += ex * ex + ey * ey + ez * ez;
+        uu += double(ux[k]) * double(ux[k]) + double(uy[k]) * double(uy[k]) +
+              double(uz[k]) * double(uz[k]);
+        dr += double(rh[k]) - double(a.C.rho0);
+        const double chk = double(rh[k]) + double(ux[k]) + double(uy[k]) + double(uz[k]);
+        bad |= !(chk == chk) || !(fabs(chk) < 1e30) ||
+               !(double(rh[k]) > 0.5 && double(rh[k]) < 2.0);
+      }
+    }
+  }
+  if (CHECK) {
+    __shared__ double smem[32];
+    block_sum_add(du2, &a.cb.acc[0], smem);
+    block_sum_add(uu, &a.cb.acc[1], smem);
+    block_sum_add(dr, &a.cb.acc[2], smem);
+    if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(a.cb.flag, 1);
   }
 }
 
@@ -265,17 +446,64 @@ __global__ void import_kernel(const double* __restrict__ in, Geom g, double rho0
 // ---- host-side launchers, instantiated once per storage type --------------
 template <typename S, typename R>
 cudaError_t launch_step_t(const void* src, void* dst, const Geom& g, const PhysParams& P,
-                          const CheckBufs& cb, bool check, dim3 block, cudaStream_t st) {
-  dim3 grid((g.nx + block.x - 1) / block.x, (g.ny + block.y - 1) / block.y, g.nz);
+                          const CheckBufs& cb, bool check, dim3 block, int npt,
+                          cudaStream_t st) {
+  StepArgs<S, R> a;
   const S* s = static_cast<const S*>(src);
   S* d = static_cast<S*>(dst);
-  if (P.has_force) {
-    if (check) step_kernel<S, R, true, true><<<grid, block, 0, st>>>(s, d, g, P, cb);
-    else step_kernel<S, R, true, false><<<grid, block, 0, st>>>(s, d, g, P, cb);
-  } else {
-    if (check) step_kernel<S, R, false, true><<<grid, block, 0, st>>>(s, d, g, P, cb);
-    else step_kernel<S, R, false, false><<<grid, block, 0, st>>>(s, d, g, P, cb);
+  for (int q = 0; q < Q; ++q) {
+    const int64_t off = int64_t(cz(q)) * g.plane + int64_t(cy(q)) * g.pitch + cx(q);
+    // address arithmetic through integers: the shifted base may precede the
+    // buffer, only base + i of a node in the box is dereferenced
+    a.srcq[q] = reinterpret_cast<const S*>(reinterpret_cast<uintptr_t>(s) +
+                                            (int64_t(q) * g.qstride - off) * int64_t(sizeof(S)));
+    a.dstq[q] = d + int64_t(q) * g.qstride;
+    a.lidc[q] = R(6.0 * wt<double>(q) * g.rho0 *
+                  (cx(q) * g.U[0] + cy(q) * g.U[1] + cz(q) * g.U[2]));
   }
+  a.src = s;
+  a.qstride = g.qstride;
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.nz = g.nz;
+  a.pitch = g.pitch;
+  a.plane = int(g.plane);
+  a.facebits = g.facebits;
+  a.C = make_const<R>(P);
+  a.cb = cb;
+  // npt: 1 or 2 nodes per thread; +4 selects the register-capped variant.
+  const bool cap = (npt & 4) != 0;
+  npt &= 3;
+#define CLBM_STEP_LAUNCH(KERNEL, GRID, ...)                                                 \
+  do {                                                                                     \
+    if (P.has_force) {                                                                     \
+      if (check) {                                                                         \
+        if (cap) KERNEL<__VA_ARGS__, true, true, true><<<GRID, block, 0, st>>>(a);         \
+        else KERNEL<__VA_ARGS__, true, true, false><<<GRID, block, 0, st>>>(a);            \
+      } else {                                                                             \
+        if (cap) KERNEL<__VA_ARGS__, true, false, true><<<GRID, block, 0, st>>>(a);        \
+        else KERNEL<__VA_ARGS__, true, false, false><<<GRID, block, 0, st>>>(a);           \
+      }                                                                                    \
+    } else {                                                                               \
+      if (check) {                                                                         \
+        if (cap) KERNEL<__VA_ARGS__, false, true, true><<<GRID, block, 0, st>>>(a);        \
+        else KERNEL<__VA_ARGS__, false, true, false><<<GRID, block, 0, st>>>(a);           \
+      } else {                                                                             \
+        if (cap) KERNEL<__VA_ARGS__, false, false, true><<<GRID, block, 0, st>>>(a);       \
+        else KERNEL<__VA_ARGS__, false, false, false><<<GRID, block, 0, st>>>(a);          \
+      }                                                                                    \
+    }                                                                                      \
+  } while (0)
+  if constexpr (std::is_same<R, float>::value) {
+    if (npt == 2) {
+      dim3 grid2((g.nx + block.x - 1) / block.x, (g.ny + 2 * block.y - 1) / (2 * block.y), g.nz);
+      CLBM_STEP_LAUNCH(step2_kernel, grid2, S);
+      return cudaGetLastError();
+    }
+  }
+  dim3 grid((g.nx + block.x - 1) / block.x, (g.ny + block.y - 1) / block.y, g.nz);
+  CLBM_STEP_LAUNCH(step_kernel, grid, S, R);
+#undef CLBM_STEP_LAUNCH
   return cudaGetLastError();
 }
 
@@ -328,8 +556,8 @@ cudaError_t launch_import_t(const double* in, const Geom& g, double rho0, double
   namespace clbm {                                                                            \
   cudaError_t launch_step_##SUFFIX(const void* src, void* dst, const Geom& g,                 \
                                    const PhysParams& P, const CheckBufs& cb, bool check,      \
-                                   dim3 block, cudaStream_t st) {                             \
-    return launch_step_t<S, R>(src, dst, g, P, cb, check, block, st);                         \
+                                   dim3 block, int npt, cudaStream_t st) {                    \
+    return launch_step_t<S, R>(src, dst, g, P, cb, check, block, npt, st);                    \
   }                                                                                           \
   cudaError_t launch_fields_##SUFFIX(const void* src, const Geom& g, const PhysParams& P,     \
                                      double* rho, double* u, double* gd, cudaStream_t st) {   \

@@ -47,7 +47,7 @@ struct CheckBufs {
 #define CLBM_DECLARE_LAUNCHERS(SUFFIX)                                                        \
   cudaError_t launch_step_##SUFFIX(const void* src, void* dst, const Geom& g,                 \
                                    const PhysParams& P, const CheckBufs& cb, bool check,      \
-                                   dim3 block, cudaStream_t st);                              \
+                                   dim3 block, int npt, cudaStream_t st);                     \
   cudaError_t launch_fields_##SUFFIX(const void* src, const Geom& g, const PhysParams& P,     \
                                      double* rho, double* u, double* gd, cudaStream_t st);    \
   cudaError_t launch_collide_nodes_##SUFFIX(const PhysParams& P, const double* fin,           \

@@ -121,24 +121,38 @@ def test_channel_f64_1000_steps(clbm, oracle):
     assert np.abs(gd_gpu - gd_ref).max() <= 1e-10 * gd_ref.max()
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s"])
-def test_ragged_mixed_boundaries_random_state(clbm, oracle, dtype):
+_MIXED = wl.Problem("mixed", 33, 17, 9, (wl.WALL, wl.WALL, wl.WALL, wl.LID, wl.PERIODIC, wl.PERIODIC),
+                    K=0.01, n=0.7, U_lid=(0.04, 0.0, 0.02), body_force=(1e-5, 0.0, -2e-6))
+
+
+@pytest.fixture(scope="module")
+def mixed_reference(oracle):
     # 33 x 17 x 9: ragged against every tile shape; walls on x, wall + lid on
-    # y, periodic z; a random perturbed initial state.
-    prob = wl.Problem("mixed", 33, 17, 9, (wl.WALL, wl.WALL, wl.WALL, wl.LID, wl.PERIODIC, wl.PERIODIC),
-                      K=0.01, n=0.7, U_lid=(0.04, 0.0, 0.02), body_force=(1e-5, 0.0, -2e-6))
-    p = _oracle_params(oracle, prob)
+    # y, periodic z; a random perturbed initial state; 200 oracle steps.
+    p = _oracle_params(oracle, _MIXED)
     r = wl.noise((19, 9, 17, 33), seed=5, amp=0.05)
-    with _lattice(clbm, prob, dtype) as lat:
-        rest = lat.get_state()
-        f0 = rest * (1 + r)
-        lat.set_state(f0)
-        lat.step(200)
-        _, u_gpu, _ = lat.fields()
     rest_o = oracle.rest_state(p)
-    assert np.array_equal(rest, rest_o)
     f_ref = oracle.run(p, rest_o * (1 + r), 200)
     _, u_ref, _ = oracle.fields(p, f_ref)
+    return r, rest_o, u_ref
+
+
+# (block_x, block_y, nodes per thread); npt = 2 collides rows y, y+1 together
+SHAPES = {"f64": [(32, 4, 1), (64, 2, 1), (128, 1, 1), (32, 8, 1)],
+          "f32": [(32, 4, 1), (128, 2, 1), (32, 4, 2), (64, 2, 2), (128, 1, 2), (32, 2, 2)],
+          "f16s": [(32, 4, 1), (32, 4, 2), (64, 1, 2)]}
+
+
+@pytest.mark.parametrize("dtype,shape", [(d, s) for d in SHAPES for s in SHAPES[d]])
+def test_ragged_mixed_boundaries_random_state(clbm, mixed_reference, dtype, shape):
+    r, rest_o, u_ref = mixed_reference
+    with _lattice(clbm, _MIXED, dtype) as lat:
+        lat.set_launch(*shape)
+        rest = lat.get_state()
+        assert np.array_equal(rest, rest_o)
+        lat.set_state(rest * (1 + r))
+        lat.step(200)
+        _, u_gpu, _ = lat.fields()
     err = np.abs(u_gpu - u_ref).max() / 0.04
     l2 = np.linalg.norm(u_gpu - u_ref) / np.linalg.norm(u_ref)
     if dtype == "f64":
@@ -147,6 +161,24 @@ def test_ragged_mixed_boundaries_random_state(clbm, oracle, dtype):
         assert l2 <= 1e-4
     else:
         assert l2 <= 2e-3
+
+
+def test_autotune_restores_state_and_keeps_parity(clbm):
+    prob = wl.cavity(40, 200.0, 0.6, dims=(40, 36, 20))
+    with _lattice(clbm, prob, "f32") as lat, _lattice(clbm, prob, "f32") as ref:
+        ref.set_launch(32, 4, 1)
+        lat.step(50)
+        ref.step(50)
+        f0 = lat.get_state()
+        info = lat.autotune(5)
+        assert info["npt"] in (1, 2) and info["us_per_step"] > 0
+        assert np.array_equal(lat.get_state(), f0)
+        assert lat.steps_done() == 50
+        lat.step(150)
+        ref.step(150)
+        _, u1, _ = lat.fields()
+        _, u2, _ = ref.fields()
+    assert np.linalg.norm(u1 - u2) / np.linalg.norm(u2) <= 1e-5
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32", "f16s"])

@@ -6,9 +6,10 @@ code that must not stall on the allocator).  They pass their own population,
 velocity and result buffers, and the library keeps its reduction scratch in a
 fixed array of its own.  This file checks that entry point against the
 handle-based clbm_step() at its check steps, on two calls in a row, within
-the tolerances of the other parity tests (FP64 1e-14, FP32 1e-6 per
-population; FP64 reductions to 1e-12 relative).  It is named so that pytest
-collects it last.
+the tolerances of the other parity tests: FP64 1e-14 and FP32 1e-6 per
+population, so the mass may differ by at most 19 N times that; the residual
+to 1e-12 (FP64) and 1e-4 (FP32, the FP32 velocity tolerance) relative.  It
+is named so that pytest collects it last.
 """
 import math
 
@@ -20,6 +21,7 @@ from paper_1908_05396_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-14, "f32": 1e-6}
+RTOL = {"f64": 1e-12, "f32": 1e-4}
 
 
 @pytest.fixture(scope="module")
@@ -66,14 +68,14 @@ def test_noalloc_matches_check_steps(clbm, dtype):
         assert np.abs(f_new - f_ref).max() <= TOL[dtype]
         s = stats.cpu().numpy()
         assert s[3] == 0.0
-        assert abs(N * 1.0 + s[2] - lat.mass()) <= 1e-12 * N
+        assert abs(N * 1.0 + s[2] - lat.mass()) <= 19 * N * TOL[dtype]
         R_ref, rc_ref = lat.residual()
         assert rc_ref == clbm.OK
         if call == 0:
             assert math.isinf(R_ref)
         else:
             R = math.sqrt(s[0]) / math.sqrt(s[1])     # check interval 1
-            assert abs(R - R_ref) <= 1e-12 * R_ref
+            assert abs(R - R_ref) <= RTOL[dtype] * R_ref
     lat.close()
 
 
