@@ -155,6 +155,48 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
  * npt = 1 or 2 nodes per thread (2 only for the FP32 and F16S forms). */
 int clbm_set_launch(clbm_handle h, int block_x, int block_y, int npt);
 
+/* ---- Batched stepping of many lattices --------------------------------
+ * Not in the paper: a batch steps up to `capacity` lattices of one storage
+ * form together, one launch of a persistent kernel per time step for all of
+ * them (tiles of every lattice from a device-side table), with each whole
+ * check interval queued as one CUDA graph.  Lattices join and leave between
+ * clbm_batch_step() calls; each keeps its own buffers, parameters, step
+ * count and residual.  While a lattice is in a batch, clbm_step() on it
+ * fails; clbm_fields/get_state/residual/... on it first wait for the batch.
+ * Destroying a lattice removes it from its batch. */
+typedef struct clbm_batch_ctx* clbm_batch;
+
+/* capacity: at most this many lattices at once (1..65536); check_interval:
+ * even number of steps between residual checks (0 -> 100); stream: CUDA
+ * stream for the batch's work (NULL -> library-owned). */
+int clbm_batch_create(clbm_dtype dtype, int capacity, int check_interval, void* stream,
+                      clbm_batch* out);
+/* Attach h (same dtype and device, not in another batch, 19 x padded nodes
+ * < 2^31); its queued work is waited for; *slot receives its slot. */
+int clbm_batch_add(clbm_batch b, clbm_handle h, int* slot);
+/* Detach the lattice in `slot` (waits for the batch's queued work). */
+int clbm_batch_remove(clbm_batch b, int slot);
+int clbm_batch_detach(clbm_batch b, clbm_handle h);
+/* Queue nsteps steps of every attached lattice (Eqs. cascadedstreaming1,
+ * cascadedcollision1).  Every step whose batch index is a multiple of the
+ * check interval is a check step for all of them. */
+int clbm_batch_step(clbm_batch b, int64_t nsteps);
+/* Results of the last check of the lattice in `slot`: residual (as
+ * clbm_residual; +Inf until it has had two checks in this batch), mass, the
+ * divergence flag and its step count.  Any pointer may be NULL.  Syncs. */
+int clbm_batch_stats(clbm_batch b, int slot, double* residual, double* mass, int* diverged,
+                     int64_t* steps);
+/* Launch shape: thread block (multiple of 32 threads, <= 256), planes per
+ * tile zc >= 1, resident blocks per SM of the persistent grid. */
+int clbm_batch_set_launch(clbm_batch b, int block_x, int block_y, int zc, int blocks_per_sm);
+/* Time block shapes x zc x blocks-per-SM on the attached lattices (states
+ * saved and restored) and keep the fastest. */
+int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int* zc,
+                        int* blocks_per_sm, double* us_per_step);
+int clbm_batch_sync(clbm_batch b);
+int clbm_batch_destroy(clbm_batch b);
+const char* clbm_batch_last_error(clbm_batch b);
+
 /* Text of the last error on h (never NULL); h may be NULL for errors of
  * clbm_create. */
 const char* clbm_last_error(clbm_handle h);

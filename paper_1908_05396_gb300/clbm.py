@@ -260,3 +260,96 @@ def step_noalloc(nx, ny, nz, face, K, n, U_lid, body_force, dtype, src, dst, u_p
 def last_error() -> str:
     msg = lib().clbm_last_error(None)
     return msg.decode() if msg else ""
+
+
+class Batch:
+    """Many lattices of one storage form stepped together (``clbm_batch``)."""
+
+    def __init__(self, dtype="f32", capacity=64, check_interval=100, stream=None):
+        L = lib()
+        if not hasattr(L, "_batch_ready"):
+            B = ctypes.c_void_p
+            L.clbm_batch_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.POINTER(B)]
+            L.clbm_batch_add.argtypes = [B, _H, ctypes.POINTER(ctypes.c_int)]
+            L.clbm_batch_remove.argtypes = [B, ctypes.c_int]
+            L.clbm_batch_detach.argtypes = [B, _H]
+            L.clbm_batch_step.argtypes = [B, ctypes.c_int64]
+            L.clbm_batch_stats.argtypes = [B, ctypes.c_int, _D, _D, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int64)]
+            L.clbm_batch_set_launch.argtypes = [B, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.c_int]
+            L.clbm_batch_autotune.argtypes = [B, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4 + [_D]
+            L.clbm_batch_sync.argtypes = [B]
+            L.clbm_batch_destroy.argtypes = [B]
+            L.clbm_batch_last_error.argtypes = [B]
+            L.clbm_batch_last_error.restype = ctypes.c_char_p
+            for n in ("clbm_batch_create", "clbm_batch_add", "clbm_batch_remove", "clbm_batch_detach",
+                      "clbm_batch_step", "clbm_batch_stats", "clbm_batch_set_launch",
+                      "clbm_batch_autotune", "clbm_batch_sync", "clbm_batch_destroy"):
+                getattr(L, n).restype = ctypes.c_int
+            L._batch_ready = True
+        self._b = ctypes.c_void_p()
+        code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        self.check_interval = int(check_interval)
+        self._bcheck(L.clbm_batch_create(code, int(capacity), int(check_interval), stream,
+                                         ctypes.byref(self._b)), create=True)
+        self.members = {}
+
+    def _bcheck(self, rc, create=False):
+        if rc != OK:
+            L = lib()
+            msg = L.clbm_last_error(None) if create else L.clbm_batch_last_error(self._b)
+            raise CLBMError(rc, msg.decode() if msg else "")
+
+    def add(self, lat: "Lattice") -> int:
+        slot = ctypes.c_int()
+        self._bcheck(lib().clbm_batch_add(self._b, lat.handle, ctypes.byref(slot)))
+        self.members[slot.value] = lat
+        return slot.value
+
+    def remove(self, slot: int) -> "Lattice":
+        self._bcheck(lib().clbm_batch_remove(self._b, int(slot)))
+        return self.members.pop(slot)
+
+    def step(self, nsteps: int) -> None:
+        self._bcheck(lib().clbm_batch_step(self._b, int(nsteps)))
+
+    def stats(self, slot: int) -> dict:
+        R, m = ctypes.c_double(), ctypes.c_double()
+        dv, st = ctypes.c_int(), ctypes.c_int64()
+        self._bcheck(lib().clbm_batch_stats(self._b, int(slot), ctypes.byref(R), ctypes.byref(m),
+                                            ctypes.byref(dv), ctypes.byref(st)))
+        return dict(residual=R.value, mass=m.value, diverged=bool(dv.value), steps=st.value)
+
+    def set_launch(self, block_x, block_y, zc, blocks_per_sm) -> None:
+        self._bcheck(lib().clbm_batch_set_launch(self._b, int(block_x), int(block_y), int(zc),
+                                                 int(blocks_per_sm)))
+
+    def autotune(self, steps: int = 6) -> dict:
+        v = [ctypes.c_int() for _ in range(4)]
+        us = ctypes.c_double()
+        self._bcheck(lib().clbm_batch_autotune(self._b, int(steps), *[ctypes.byref(x) for x in v],
+                                               ctypes.byref(us)))
+        return dict(block=(v[0].value, v[1].value), zc=v[2].value, blocks_per_sm=v[3].value,
+                    us_per_step=us.value)
+
+    def sync(self) -> None:
+        self._bcheck(lib().clbm_batch_sync(self._b))
+
+    def close(self) -> None:
+        if getattr(self, "_b", None):
+            lib().clbm_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,487 @@
+// clbm_batch.cu -- host side of the batched multi-lattice step (include/clbm.h).
+//
+// A batch holds up to `capacity` lattices (clbm_handle) of one storage form
+// and steps them together: one launch of the persistent batch kernel per time
+// step, for all of them.  Whole check intervals run as one CUDA graph captured
+// on first use: (check_interval - 1) plain launches of alternating parity,
+// then a check launch whose per-lattice FP64 sums are copied to pinned host
+// memory.  The kernel reads its tile table and lattice descriptors from device
+// memory, so the graph stays valid when lattices join or leave; only a change
+// of launch shape or of the table's capacity recaptures it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/clbm.h"
+#include "ctx.h"
+#include "launch.h"
+
+using namespace clbm;
+
+struct clbm_batch_ctx {
+  int device = 0;
+  clbm_dtype dtype = CLBM_F32;
+  int capacity = 0;
+  int check_interval = 100;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<clbm_ctx*> slots;
+  std::vector<int64_t> slot_checks;   // checks run since the lattice joined
+  std::vector<int64_t> slot_joined;   // batch step at which it joined
+  size_t desc_bytes = 0;
+  void* d_desc = nullptr;             // capacity descriptors
+  int* d_owner = nullptr;             // tile -> lattice index
+  int owner_cap = 0;
+  BatchHeader* d_hdr = nullptr;
+  double* d_acc = nullptr;            // capacity x 4
+  double* h_acc = nullptr;            // pinned copy
+  void* h_stage = nullptr;            // pinned staging of descriptors
+  std::vector<int> h_owner;
+  int parity = 0;                     // steps since the tables were written, mod 2
+  int64_t steps = 0;
+  bool dirty = true;
+  dim3 block{32, 4, 1};
+  int zc = 4;
+  int blocks_per_sm = 4;
+  int sms = 1;
+  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t check_done = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int bfail(clbm_batch_ctx* b, int code, const std::string& m) {
+  if (b) b->err = m;
+  clbm::set_unbound_error(m.c_str());
+  return code;
+}
+
+#define BCK(b, expr)                                                                        \
+  do {                                                                                      \
+    cudaError_t e_ = (expr);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return bfail(b, e_ == cudaErrorMemoryAllocation ? CLBM_ERR_OOM : CLBM_ERR_CUDA,        \
+                   std::string(#expr) + ": " + cudaGetErrorString(e_));                      \
+  } while (0)
+
+size_t desc_size(clbm_dtype t) {
+  return t == CLBM_F64 ? desc_size_f64() : t == CLBM_F32 ? desc_size_f32() : desc_size_f16();
+}
+
+void fill_desc(clbm_dtype t, void* out, const clbm_ctx* h, int tx, int ty, int tb, int slot) {
+  const void* cur = h->buf[h->cur];
+  const void* other = h->buf[1 - h->cur];
+  if (t == CLBM_F64) fill_desc_f64(out, h->g, h->P, cur, other, h->uprev, tx, ty, tb, slot);
+  else if (t == CLBM_F32) fill_desc_f32(out, h->g, h->P, cur, other, h->uprev, tx, ty, tb, slot);
+  else fill_desc_f16(out, h->g, h->P, cur, other, h->uprev, tx, ty, tb, slot);
+}
+
+cudaError_t launch(clbm_batch_ctx* b, bool check) {
+  const int grid = b->blocks_per_sm * b->sms;
+  switch (b->dtype) {
+    case CLBM_F64:
+      return launch_batch_f64(b->d_desc, b->d_owner, b->d_hdr, b->parity, check, b->d_acc,
+                              b->block, grid, b->stream);
+    case CLBM_F32:
+      return launch_batch_f32(b->d_desc, b->d_owner, b->d_hdr, b->parity, check, b->d_acc,
+                              b->block, grid, b->stream);
+    default:
+      return launch_batch_f16(b->d_desc, b->d_owner, b->d_hdr, b->parity, check, b->d_acc,
+                              b->block, grid, b->stream);
+  }
+}
+
+void drop_graph(clbm_batch_ctx* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+}
+
+// Rebuild and upload the tables from the attached lattices' current state.
+int upload(clbm_batch_ctx* b) {
+  BCK(b, cudaStreamSynchronize(b->stream));  // staging buffers and tables are free
+  int ntiles = 0, nlat = 0;
+  std::vector<int> first;
+  b->h_owner.clear();
+  char* stage = static_cast<char*>(b->h_stage);
+  for (int s = 0; s < b->capacity; ++s) {
+    clbm_ctx* h = b->slots[s];
+    if (!h) continue;
+    const int tx = (h->g.nx + int(b->block.x) - 1) / int(b->block.x);
+    const int ty = (h->g.ny + int(b->block.y) - 1) / int(b->block.y);
+    const int tz = (h->g.nz + b->zc - 1) / b->zc;
+    fill_desc(b->dtype, stage + size_t(nlat) * b->desc_bytes, h, tx, ty, ntiles, s);
+    const int n = tx * ty * tz;
+    b->h_owner.insert(b->h_owner.end(), size_t(n), nlat);
+    ntiles += n;
+    ++nlat;
+  }
+  if (ntiles > b->owner_cap) {
+    if (b->d_owner) BCK(b, cudaFree(b->d_owner));
+    b->d_owner = nullptr;
+    const int cap = std::max(ntiles, 2 * b->owner_cap);
+    BCK(b, cudaMalloc(reinterpret_cast<void**>(&b->d_owner), size_t(cap) * sizeof(int)));
+    b->owner_cap = cap;
+    drop_graph(b);  // the graph holds the old table address
+  }
+  BatchHeader hdr{nlat, ntiles, b->zc, 0};
+  if (nlat)
+    BCK(b, cudaMemcpy(b->d_desc, stage, size_t(nlat) * b->desc_bytes, cudaMemcpyHostToDevice));
+  if (ntiles)
+    BCK(b, cudaMemcpy(b->d_owner, b->h_owner.data(), size_t(ntiles) * sizeof(int),
+                      cudaMemcpyHostToDevice));
+  BCK(b, cudaMemcpy(b->d_hdr, &hdr, sizeof(hdr), cudaMemcpyHostToDevice));
+  b->parity = 0;
+  b->dirty = false;
+  return CLBM_OK;
+}
+
+// Advance the host-side bookkeeping of the attached handles by n steps.
+void advance(clbm_batch_ctx* b, int64_t n) {
+  for (clbm_ctx* h : b->slots)
+    if (h) {
+      h->steps += n;
+      if (n & 1) h->cur = 1 - h->cur;
+    }
+  b->steps += n;
+}
+
+int one_step(clbm_batch_ctx* b) {
+  const bool check = ((b->steps + 1) % b->check_interval) == 0;
+  if (check) BCK(b, cudaMemsetAsync(b->d_acc, 0, size_t(b->capacity) * 4 * sizeof(double), b->stream));
+  BCK(b, launch(b, check));
+  b->parity ^= 1;
+  if (check) {
+    BCK(b, cudaMemcpyAsync(b->h_acc, b->d_acc, size_t(b->capacity) * 4 * sizeof(double),
+                           cudaMemcpyDeviceToHost, b->stream));
+    BCK(b, cudaEventRecord(b->check_done, b->stream));
+    for (int s = 0; s < b->capacity; ++s)
+      if (b->slots[s]) b->slot_checks[s] += 1;
+  }
+  advance(b, 1);
+  return CLBM_OK;
+}
+
+// Capture one check interval as a graph (parity 0 at its start).
+int capture(clbm_batch_ctx* b) {
+  drop_graph(b);
+  cudaGraph_t g = nullptr;
+  BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  int par = 0;
+  for (int k = 0; k < b->check_interval && e == cudaSuccess; ++k) {
+    const bool check = k == b->check_interval - 1;
+    if (check)
+      e = cudaMemsetAsync(b->d_acc, 0, size_t(b->capacity) * 4 * sizeof(double), b->stream);
+    const int keep = b->parity;
+    b->parity = par;
+    if (e == cudaSuccess) e = launch(b, check);
+    b->parity = keep;
+    par ^= 1;
+    if (check && e == cudaSuccess)
+      e = cudaMemcpyAsync(b->h_acc, b->d_acc, size_t(b->capacity) * 4 * sizeof(double),
+                          cudaMemcpyDeviceToHost, b->stream);
+    if (check && e == cudaSuccess) e = cudaEventRecord(b->check_done, b->stream);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->graph = nullptr;
+    return bfail(b, CLBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  return CLBM_OK;
+}
+
+bool valid(const clbm_batch_ctx* b) { return b && b->d_desc; }
+
+// The kernel skips any tile whose descriptor fails its checks and sets the
+// header's error word; report that instead of silently wrong results.
+int check_tables(clbm_batch_ctx* b) {
+  BatchHeader hdr{};
+  BCK(b, cudaMemcpy(&hdr, b->d_hdr, sizeof(hdr), cudaMemcpyDeviceToHost));
+  if (hdr.err) return bfail(b, CLBM_ERR_CUDA, "batch kernel found an inconsistent tile table");
+  return CLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int clbm_batch_create(clbm_dtype dtype, int capacity, int check_interval, void* stream,
+                      clbm_batch* out) {
+  if (!out) return bfail(nullptr, CLBM_ERR_ARG, "null output");
+  *out = nullptr;
+  if (dtype != CLBM_F64 && dtype != CLBM_F32 && dtype != CLBM_F16S)
+    return bfail(nullptr, CLBM_ERR_ARG, "unknown dtype");
+  if (capacity < 1 || capacity > (1 << 16)) return bfail(nullptr, CLBM_ERR_ARG, "capacity must be in [1, 65536]");
+  if (check_interval <= 0) check_interval = 100;
+  if (check_interval % 2) return bfail(nullptr, CLBM_ERR_ARG, "check_interval must be even");
+  clbm_batch_ctx* b = new (std::nothrow) clbm_batch_ctx();
+  if (!b) return bfail(nullptr, CLBM_ERR_OOM, "host allocation failed");
+  b->dtype = dtype;
+  b->capacity = capacity;
+  b->check_interval = check_interval;
+  b->slots.assign(size_t(capacity), nullptr);
+  b->slot_checks.assign(size_t(capacity), 0);
+  b->slot_joined.assign(size_t(capacity), 0);
+  b->desc_bytes = desc_size(dtype);  // the kernel indexes the array with this stride
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess) {
+    if (stream) {
+      b->stream = static_cast<cudaStream_t>(stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+      b->own_stream = e == cudaSuccess;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_desc, size_t(capacity) * b->desc_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_hdr), sizeof(BatchHeader));
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_acc), size_t(capacity) * 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&b->h_acc), size_t(capacity) * 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_stage, size_t(capacity) * b->desc_bytes);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->check_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) std::memset(b->h_acc, 0, size_t(capacity) * 4 * sizeof(double));
+  if (e != cudaSuccess) {
+    std::string m = std::string("clbm_batch_create: ") + cudaGetErrorString(e);
+    clbm_batch_destroy(b);
+    return bfail(nullptr, e == cudaErrorMemoryAllocation ? CLBM_ERR_OOM : CLBM_ERR_CUDA, m);
+  }
+  *out = b;
+  return CLBM_OK;
+}
+
+int clbm_batch_add(clbm_batch b, clbm_handle h, int* slot) {
+  if (!valid(b) || !h || !h->buf[0]) return bfail(b, CLBM_ERR_ARG, "invalid batch or handle");
+  if (h->dtype != b->dtype) return bfail(b, CLBM_ERR_ARG, "lattice dtype differs from the batch's");
+  if (h->device != b->device) return bfail(b, CLBM_ERR_ARG, "lattice lives on another device");
+  if (h->batch) return bfail(b, CLBM_ERR_ARG, "lattice is already in a batch");
+  if (int64_t(NQ) * h->g.qstride >= (int64_t(1) << 31))
+    return bfail(b, CLBM_ERR_UNSUPPORTED, "lattice too large to batch (19 x padded nodes >= 2^31)");
+  int s = 0;
+  while (s < b->capacity && b->slots[s]) ++s;
+  if (s == b->capacity) return bfail(b, CLBM_ERR_ARG, "batch is full");
+  BCK(b, cudaSetDevice(b->device));
+  BCK(b, cudaStreamSynchronize(h->stream));  // the lattice's own queued work is done
+  b->slots[s] = h;
+  b->slot_checks[s] = 0;
+  b->slot_joined[s] = b->steps;
+  h->batch = b;
+  b->dirty = true;
+  if (slot) *slot = s;
+  return CLBM_OK;
+}
+
+int clbm_batch_remove(clbm_batch b, int slot) {
+  if (!valid(b) || slot < 0 || slot >= b->capacity || !b->slots[slot])
+    return bfail(b, CLBM_ERR_ARG, "invalid batch or slot");
+  BCK(b, cudaSetDevice(b->device));
+  BCK(b, cudaStreamSynchronize(b->stream));  // its last batched steps are done
+  b->slots[slot]->batch = nullptr;
+  b->slots[slot] = nullptr;
+  b->dirty = true;
+  return CLBM_OK;
+}
+
+int clbm_batch_step(clbm_batch b, int64_t nsteps) {
+  if (!valid(b) || nsteps < 0) return bfail(b, CLBM_ERR_ARG, "invalid batch or step count");
+  BCK(b, cudaSetDevice(b->device));
+  int64_t left = nsteps;
+  while (left > 0) {
+    if (b->dirty) {
+      if (int r = upload(b)) return r;
+    }
+    const int64_t ci = b->check_interval;
+    if (b->steps % ci == 0 && b->parity == 0 && left >= ci) {
+      if (!b->graph) {
+        if (int r = capture(b)) return r;
+      }
+      BCK(b, cudaGraphLaunch(b->graph, b->stream));
+      for (int s = 0; s < b->capacity; ++s)
+        if (b->slots[s]) b->slot_checks[s] += 1;
+      advance(b, ci);
+      left -= ci;
+      continue;
+    }
+    if (int r = one_step(b)) return r;
+    left -= 1;
+  }
+  return CLBM_OK;
+}
+
+int clbm_batch_stats(clbm_batch b, int slot, double* residual, double* mass, int* diverged,
+                     int64_t* steps) {
+  if (!valid(b) || slot < 0 || slot >= b->capacity || !b->slots[slot])
+    return bfail(b, CLBM_ERR_ARG, "invalid batch or slot");
+  BCK(b, cudaSetDevice(b->device));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  if (int r = check_tables(b)) return r;
+  const double* a = b->h_acc + 4 * slot;
+  clbm_ctx* h = b->slots[slot];
+  if (residual) {
+    if (b->slot_checks[slot] < 2) *residual = INFINITY;
+    else if (!(a[1] > 0.0)) *residual = a[0] == 0.0 ? 0.0 : INFINITY;
+    else *residual = std::sqrt(a[0]) / (double(b->check_interval) * std::sqrt(a[1]));
+  }
+  if (mass) *mass = double(h->g.nx) * h->g.ny * h->g.nz * h->g.rho0 + a[2];
+  int f = 0;
+  std::memcpy(&f, &a[3], sizeof(int));
+  if (b->slot_checks[slot] < 1) f = 0;
+  if (diverged) *diverged = f;
+  if (steps) *steps = h->steps;
+  return CLBM_OK;
+}
+
+int clbm_batch_set_launch(clbm_batch b, int block_x, int block_y, int zc, int blocks_per_sm) {
+  if (!valid(b)) return bfail(b, CLBM_ERR_ARG, "invalid batch");
+  if (block_x < 1 || block_y < 1 || block_x * block_y > 256 || (block_x * block_y) % 32 ||
+      zc < 1 || blocks_per_sm < 1 || blocks_per_sm > 32)
+    return bfail(b, CLBM_ERR_ARG, "bad launch shape");
+  BCK(b, cudaSetDevice(b->device));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  b->block = dim3(block_x, block_y, 1);
+  b->zc = zc;
+  b->blocks_per_sm = blocks_per_sm;
+  b->dirty = true;
+  drop_graph(b);
+  return CLBM_OK;
+}
+
+int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int* zc,
+                        int* blocks_per_sm, double* us_per_step) {
+  if (!valid(b)) return bfail(b, CLBM_ERR_ARG, "invalid batch");
+  BCK(b, cudaSetDevice(b->device));
+  if (steps <= 0) steps = 6;
+  // Save every lattice's current state: tuning runs real steps.
+  BCK(b, cudaStreamSynchronize(b->stream));
+  std::vector<void*> saved(size_t(b->capacity), nullptr);
+  std::vector<int> cur0(size_t(b->capacity), 0);
+  std::vector<int64_t> steps0(size_t(b->capacity), 0);
+  cudaError_t err = cudaSuccess;
+  for (int s = 0; s < b->capacity && err == cudaSuccess; ++s) {
+    clbm_ctx* h = b->slots[s];
+    if (!h) continue;
+    const size_t bytes = size_t(NQ) * size_t(h->g.qstride) * h->elem;
+    err = cudaMallocAsync(&saved[s], bytes, b->stream);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(saved[s], h->buf[h->cur], bytes, cudaMemcpyDeviceToDevice, b->stream);
+    cur0[s] = h->cur;
+    steps0[s] = h->steps;
+  }
+  const int64_t bsteps0 = b->steps;
+  const dim3 block0 = b->block;
+  const int zc0 = b->zc, bps0 = b->blocks_per_sm;
+  const int shapes[][2] = {{32, 2}, {32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}};
+  const int zcs[] = {1, 2, 4, 8};
+  const int bpss[] = {4, 6, 8};
+  double best = 1e300;
+  int bx = block0.x, by = block0.y, bz = zc0, bb = bps0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (err == cudaSuccess) err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  for (auto& sh : shapes)
+    for (int z : zcs)
+      for (int bp : bpss) {
+        if (err != cudaSuccess) break;
+        if (sh[0] * sh[1] * bp > 2048) continue;   // at most 2048 threads per SM
+        b->block = dim3(sh[0], sh[1], 1);
+        b->zc = z;
+        b->blocks_per_sm = bp;
+        b->dirty = true;
+        if (upload(b) != CLBM_OK) { err = cudaErrorUnknown; break; }
+        for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
+          err = launch(b, false);
+          b->parity ^= 1;
+        }
+        if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
+        for (int k = 0; k < steps && err == cudaSuccess; ++k) {
+          err = launch(b, false);
+          b->parity ^= 1;
+        }
+        if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && 1e3 * ms / steps < best) {
+          best = 1e3 * ms / steps;
+          bx = sh[0];
+          by = sh[1];
+          bz = z;
+          bb = bp;
+        }
+      }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  // Restore states, counters and the chosen shape.
+  for (int s = 0; s < b->capacity; ++s) {
+    clbm_ctx* h = b->slots[s];
+    if (!h || !saved[s]) continue;
+    h->cur = cur0[s];
+    h->steps = steps0[s];
+    const size_t bytes = size_t(NQ) * size_t(h->g.qstride) * h->elem;
+    cudaError_t e2 = cudaMemcpyAsync(h->buf[h->cur], saved[s], bytes, cudaMemcpyDeviceToDevice,
+                                     b->stream);
+    if (err == cudaSuccess) err = e2;
+    cudaFreeAsync(saved[s], b->stream);
+  }
+  b->steps = bsteps0;
+  b->block = dim3(bx, by, 1);
+  b->zc = bz;
+  b->blocks_per_sm = bb;
+  b->dirty = true;
+  drop_graph(b);
+  cudaError_t e3 = cudaStreamSynchronize(b->stream);
+  if (err == cudaSuccess) err = e3;
+  if (err != cudaSuccess)
+    return bfail(b, CLBM_ERR_CUDA, std::string("clbm_batch_autotune: ") + cudaGetErrorString(err));
+  if (block_x) *block_x = bx;
+  if (block_y) *block_y = by;
+  if (zc) *zc = bz;
+  if (blocks_per_sm) *blocks_per_sm = bb;
+  if (us_per_step) *us_per_step = best;
+  return CLBM_OK;
+}
+
+int clbm_batch_sync(clbm_batch b) {
+  if (!valid(b)) return bfail(b, CLBM_ERR_ARG, "invalid batch");
+  BCK(b, cudaSetDevice(b->device));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  return check_tables(b);
+}
+
+int clbm_batch_destroy(clbm_batch b) {
+  if (!b) return CLBM_OK;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (clbm_ctx* h : b->slots)
+    if (h) h->batch = nullptr;
+  drop_graph(b);
+  if (b->d_desc) cudaFree(b->d_desc);
+  if (b->d_owner) cudaFree(b->d_owner);
+  if (b->d_hdr) cudaFree(b->d_hdr);
+  if (b->d_acc) cudaFree(b->d_acc);
+  if (b->h_acc) cudaFreeHost(b->h_acc);
+  if (b->h_stage) cudaFreeHost(b->h_stage);
+  if (b->check_done) cudaEventDestroy(b->check_done);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return CLBM_OK;
+}
+
+const char* clbm_batch_last_error(clbm_batch b) { return b ? b->err.c_str() : ""; }
+
+int clbm_batch_detach(clbm_batch b, clbm_handle h) {
+  if (!valid(b) || !h) return bfail(b, CLBM_ERR_ARG, "invalid batch or handle");
+  for (int s = 0; s < b->capacity; ++s)
+    if (b->slots[s] == h) return clbm_batch_remove(b, s);
+  return bfail(b, CLBM_ERR_ARG, "lattice is not in this batch");
+}
+
+}  // extern "C"

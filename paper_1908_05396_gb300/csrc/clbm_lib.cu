@@ -17,34 +17,11 @@
 #include <vector>
 
 #include "../../include/clbm.h"
+#include "ctx.h"
 #include "launch.h"
 
 using namespace clbm;
 
-struct clbm_ctx {
-  int device = 0;
-  clbm_domain dom{};
-  clbm_dtype dtype = CLBM_F64;
-  Geom g{};
-  PhysParams P{};
-  size_t elem = 8;       // bytes per stored population
-  size_t rsize = 8;      // bytes per math-precision value
-  void* buf[2] = {nullptr, nullptr};
-  int cur = 0;           // buffer holding the current state
-  void* uprev = nullptr;
-  double* acc = nullptr; // device: 3 doubles, then the int flag
-  int* flag = nullptr;
-  double* host = nullptr; // pinned: acc[3], flag as double
-  cudaEvent_t check_done = nullptr;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int64_t steps = 0;
-  int64_t checks = 0;    // check steps queued so far
-  bool diverged = false; // sticky once a completed check saw divergence
-  dim3 block{32, 4, 1};
-  int npt = 1;           // nodes per thread (1 or 2), + 4 for the register-capped kernel
-  std::string err;
-};
 
 namespace {
 
@@ -82,6 +59,11 @@ cudaError_t dispatch_step(clbm_ctx* h, bool check) {
 
 int set_device(clbm_ctx* h) {
   CK(h, cudaSetDevice(h->device));
+  // A batched lattice is written on the batch's stream: let it finish first.
+  if (h->batch) {
+    int r = clbm_batch_sync(h->batch);
+    if (r != CLBM_OK) return fail(h, r, "batch: " + std::string(clbm_last_error(nullptr)));
+  }
   return CLBM_OK;
 }
 
@@ -191,7 +173,7 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
   h->block.x = d->nx <= 32 ? 32 : d->nx <= 64 ? 64 : 128;
   h->block.y = 128 / h->block.x;
   h->block.z = 1;
-  h->npt = dtype == CLBM_F64 ? 1 : 2;
+  h->npt = 1;  // the autotuner may switch to two nodes per thread
 
   auto cleanup = [&](int code, const std::string& m) {
     g_create_err = m + (h->err.empty() ? "" : (": " + h->err));
@@ -236,6 +218,7 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
 int clbm_step(clbm_handle h, int64_t nsteps) {
   if (bad(h)) return fail(h, CLBM_ERR_ARG, "invalid handle");
   if (nsteps < 0) return fail(h, CLBM_ERR_ARG, "nsteps must be >= 0");
+  if (h->batch) return fail(h, CLBM_ERR_ARG, "lattice is in a batch: step the batch");
   if (int r = set_device(h)) return r;
   const int64_t every = h->dom.check_interval;
   for (int64_t s = 0; s < nsteps; ++s) {
@@ -505,6 +488,7 @@ int clbm_set_launch(clbm_handle h, int block_x, int block_y, int npt) {
 
 int clbm_destroy(clbm_handle h) {
   if (!h) return CLBM_OK;
+  if (h->batch) clbm_batch_detach(h->batch, h);
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (int b = 0; b < 2; ++b)

@@ -1,0 +1,40 @@
+// ctx.h -- the handle behind clbm_handle, shared by the host translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/clbm.h"
+#include "launch.h"
+
+struct clbm_ctx {
+  int device = 0;
+  clbm_domain dom{};
+  clbm_dtype dtype = CLBM_F64;
+  clbm::Geom g{};
+  clbm::PhysParams P{};
+  size_t elem = 8;       // bytes per stored population
+  size_t rsize = 8;      // bytes per math-precision value
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;           // buffer holding the current state
+  void* uprev = nullptr;
+  double* acc = nullptr; // device: 3 doubles, then the int flag
+  int* flag = nullptr;
+  double* host = nullptr; // pinned: acc[3], flag as double
+  cudaEvent_t check_done = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t steps = 0;
+  int64_t checks = 0;    // check steps queued so far
+  bool diverged = false; // sticky once a completed check saw divergence
+  dim3 block{32, 4, 1};
+  int npt = 1;           // nodes per thread (1 or 2), + 4 for the register-capped kernel
+  struct clbm_batch_ctx* batch = nullptr;  // batch stepping this lattice, if any
+  std::string err;
+};
+
+namespace clbm {
+// Queue one step of a handle (clbm_lib.cu).
+cudaError_t handle_dispatch_step(clbm_ctx* h, bool check);
+}  // namespace clbm

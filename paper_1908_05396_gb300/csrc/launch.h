@@ -61,6 +61,24 @@ struct CheckBufs {
 // Record the text that clbm_last_error(NULL) returns on this thread.
 void set_unbound_error(const char* msg);
 
+// Batched step (batch.cuh): descriptors are opaque bytes to the host code.
+struct BatchHeader {
+  int nlat;
+  int ntiles;
+  int zc;   // planes per tile
+  int err;  // set by the kernel if a tile's descriptor fails its checks
+};
+#define CLBM_DECLARE_BATCH(SUFFIX)                                                              \
+  cudaError_t launch_batch_##SUFFIX(const void* lats, const int* owner, const void* hdr,        \
+                                    int parity, bool check, double* acc, dim3 block, int grid,  \
+                                    cudaStream_t st);                                           \
+  size_t desc_size_##SUFFIX();                                                                  \
+  void fill_desc_##SUFFIX(void* out, const Geom& g, const PhysParams& P, const void* cur,       \
+                          const void* other, void* uprev, int tx, int ty, int tb, int slot);
+CLBM_DECLARE_BATCH(f64)
+CLBM_DECLARE_BATCH(f32)
+CLBM_DECLARE_BATCH(f16)
+
 CLBM_DECLARE_LAUNCHERS(f64)
 CLBM_DECLARE_LAUNCHERS(f32)
 CLBM_DECLARE_LAUNCHERS(f16)

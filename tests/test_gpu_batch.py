@@ -1,0 +1,133 @@
+"""Batched stepping: many uneven lattices in one persistent launch must give
+the same result as each lattice stepped alone (same storage form), including
+lattices that join and leave while others run, and the per-lattice residuals
+of the batch's check steps must match the lone lattices'.
+
+FP64 results are bitwise identical.  The FP32-math forms agree to FP32
+rounding (nvcc may fuse a different set of multiply-adds in the batch
+kernel's force path): 1e-6 per population for FP32 storage, one FP16 ulp of
+the stored deviation for F16S."""
+import numpy as np
+import pytest
+
+from paper_1908_05396_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def clbm():
+    from paper_1908_05396_gb300 import build
+    build.build()
+    from paper_1908_05396_gb300 import clbm as c
+    c.lib()
+    return c
+
+
+def _mix(seed=0):
+    rng = np.random.default_rng(seed)
+    probs = []
+    for _ in range(4):
+        L = int(rng.integers(12, 40))
+        probs.append(wl.cavity(L, float(rng.uniform(50, 500)), float(rng.uniform(0.5, 1.5)),
+                               dims=(L, int(rng.integers(10, 40)), int(rng.integers(6, 30)))))
+    probs.append(wl.channel(int(rng.integers(16, 48)), 0.7, u_max=0.02, Re=20.0, nx=5, nz=3))
+    probs.append(wl.Problem("box", 17, 9, 11, (wl.PERIODIC,) * 6, K=0.02, n=1.3,
+                            body_force=(1e-5, -2e-6, 3e-6)))
+    return probs
+
+
+W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+
+
+def _same(f, f_ref, dtype):
+    if dtype == "f64":
+        assert np.array_equal(f, f_ref), np.abs(f - f_ref).max()
+    elif dtype == "f32":
+        assert np.abs(f - f_ref).max() <= 1e-6
+    else:
+        dev = np.abs(f_ref - W[:, None, None, None])
+        assert np.all(np.abs(f - f_ref) <= dev * 2.0 ** -10 + 1e-7)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s"])
+def test_batch_equals_alone(clbm, dtype):
+    probs = _mix()
+    steps = 257                      # graph chunks + single steps + odd count
+    alone = []
+    for p in probs:
+        with clbm.Lattice(**p.kwargs(), dtype=dtype, check_interval=50) as lat:
+            lat.step(steps)
+            R, _ = lat.residual()
+            alone.append((lat.get_state(), R, lat.mass()))
+    lats = [clbm.Lattice(**p.kwargs(), dtype=dtype, check_interval=50) for p in probs]
+    with clbm.Batch(dtype, capacity=8, check_interval=50) as b:
+        slots = [b.add(lt) for lt in lats]
+        b.step(steps)
+        for s, lt, (f_ref, R_ref, m_ref) in zip(slots, lats, alone):
+            st = b.stats(s)
+            assert st["steps"] == steps and not st["diverged"]
+            f = lt.get_state()
+            _same(f, f_ref, dtype)
+            rtol = 1e-12 if dtype == "f64" else 1e-4
+            assert abs(st["residual"] - R_ref) <= rtol * R_ref
+            assert abs(st["mass"] - m_ref) <= 1e-9 * m_ref
+    for lt in lats:
+        lt.close()
+
+
+def test_batch_join_and_leave(clbm):
+    probs = _mix(1)
+    counts = {}
+    lats = [clbm.Lattice(**p.kwargs(), dtype="f32", check_interval=50) for p in probs]
+    with clbm.Batch("f32", capacity=4, check_interval=50) as b:
+        s0 = b.add(lats[0])
+        s1 = b.add(lats[1])
+        b.step(120)
+        b.add(lats[2])               # joins mid-interval
+        b.step(75)
+        b.remove(s0)                 # leaves; runs on alone for a while
+        lats[0].step(33)
+        b.add(lats[3])
+        b.step(101)
+        b.remove(s1)
+        b.add(lats[0])               # re-joins
+        b.step(40)
+        for lt in lats[:4]:
+            counts[id(lt)] = lt.steps_done()
+    for p, lt in zip(probs[:4], lats[:4]):
+        n = counts[id(lt)]
+        with clbm.Lattice(**p.kwargs(), dtype="f32", check_interval=50) as ref:
+            ref.step(n)
+            _same(lt.get_state(), ref.get_state(), "f32")
+        lt.close()
+    assert counts[id(lats[0])] == 120 + 75 + 33 + 40
+    assert counts[id(lats[3])] == 101 + 40
+
+
+def test_batch_autotune_restores_state(clbm):
+    probs = _mix(2)[:3]
+    lats = [clbm.Lattice(**p.kwargs(), dtype="f32") for p in probs]
+    with clbm.Batch("f32", capacity=4) as b:
+        for lt in lats:
+            b.add(lt)
+        b.step(30)
+        before = [lt.get_state() for lt in lats]
+        info = b.autotune(3)
+        assert info["us_per_step"] > 0 and info["zc"] >= 1
+        after = [lt.get_state() for lt in lats]
+        for x, y in zip(before, after):
+            assert np.array_equal(x, y)
+        assert all(lt.steps_done() == 30 for lt in lats)
+    for lt in lats:
+        lt.close()
+
+
+def test_step_refused_while_batched(clbm):
+    lat = clbm.Lattice(**wl.cavity(10, 100.0, 1.0).kwargs(), dtype="f32")
+    with clbm.Batch("f32", capacity=2) as b:
+        b.add(lat)
+        with pytest.raises(clbm.CLBMError):
+            lat.step(1)
+    lat.step(1)                      # the batch is gone: stepping alone works again
+    lat.close()
