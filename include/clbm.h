@@ -197,6 +197,74 @@ int clbm_batch_sync(clbm_batch b);
 int clbm_batch_destroy(clbm_batch b);
 const char* clbm_batch_last_error(clbm_batch b);
 
+/* ---- Continuous-batching solve server -----------------------------------
+ * Not in the paper: a worker thread owns a batch and repeatedly (1) admits
+ * queued requests first come first served while a slot is free and the
+ * request's device memory fits the HBM budget, (2) steps every admitted
+ * lattice by one check interval in one graph launch, (3) retires lattices
+ * whose residual (as clbm_residual) is <= tol, that diverged, that reached
+ * max_steps, or whose residual has not fallen by 10 % for plateau_checks
+ * checks.  Requests join only at check-interval boundaries, so a request's
+ * step count and result do not depend on the other requests in the mix. */
+typedef struct {
+  clbm_domain dom;       /* lattice; dom.stream and dom.check_interval ignored */
+  double K, n;           /* as clbm_create */
+  double U_lid[3];
+  double body_force[3];
+  double tol;            /* residual target */
+  int64_t max_steps;     /* step cap (0: none) */
+  int plateau_checks;    /* 0: no plateau rule */
+  int keep_fields;       /* copy rho, u, gamma_dot to host memory at the end */
+} clbm_request;
+
+enum {
+  CLBM_SOLVE_CONVERGED = 0,
+  CLBM_SOLVE_MAX_STEPS = 1,
+  CLBM_SOLVE_PLATEAU = 2,
+  CLBM_SOLVE_DIVERGED = 3,
+  CLBM_SOLVE_REJECTED = 4,   /* larger than the whole budget */
+  CLBM_SOLVE_CANCELLED = 5,  /* server destroyed first */
+  CLBM_SOLVE_ERROR = 6
+};
+
+typedef struct {
+  int64_t id;
+  int status;                         /* CLBM_SOLVE_* */
+  int64_t steps;
+  double residual, mass;
+  double t_submit, t_admit, t_done;   /* seconds on the server's clock */
+  int64_t N;                          /* lattice nodes */
+} clbm_result;
+
+typedef struct {
+  int64_t queued, active, done;
+  double used_bytes;                  /* device memory held by admitted lattices */
+  double lattice_updates;             /* node updates done so far */
+  double busy_seconds;                /* time spent stepping */
+  double clock;                       /* the server clock now */
+} clbm_server_stats;
+
+typedef struct clbm_server_ctx* clbm_server;
+
+/* The server's lattices live on the device current at creation. */
+int clbm_server_create(clbm_dtype dtype, double hbm_budget_bytes, int max_active,
+                       int check_interval, clbm_server* out);
+/* Queue a request (thread-safe); *id identifies it. */
+int clbm_server_submit(clbm_server s, const clbm_request* req, int64_t* id);
+/* Block until request id is finished (timeout_s < 0: no limit); returns
+ * CLBM_ERR_TIMEOUT if it is not finished in time. */
+int clbm_server_wait(clbm_server s, int64_t id, double timeout_s, clbm_result* out);
+/* Up to max finished results (not yet released), in id order. */
+int clbm_server_results(clbm_server s, clbm_result* out, int max, int* n);
+/* Fields of a finished keep_fields request, layouts as clbm_fields. */
+int clbm_server_fields(clbm_server s, int64_t id, double* rho, double* u, double* gamma_dot);
+/* Forget a finished request and its fields. */
+int clbm_server_release(clbm_server s, int64_t id);
+int clbm_server_info(clbm_server s, clbm_server_stats* out);
+/* Stop after the current interval; unfinished requests end CANCELLED. */
+int clbm_server_destroy(clbm_server s);
+const char* clbm_server_last_error(clbm_server s);
+
 /* Text of the last error on h (never NULL); h may be NULL for errors of
  * clbm_create. */
 const char* clbm_last_error(clbm_handle h);

@@ -353,3 +353,130 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("dom", Domain), ("K", ctypes.c_double), ("n", ctypes.c_double),
+                ("U_lid", ctypes.c_double * 3), ("body_force", ctypes.c_double * 3),
+                ("tol", ctypes.c_double), ("max_steps", ctypes.c_int64),
+                ("plateau_checks", ctypes.c_int), ("keep_fields", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int), ("steps", ctypes.c_int64),
+                ("residual", ctypes.c_double), ("mass", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("N", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("active", ctypes.c_int64), ("done", ctypes.c_int64),
+                ("used_bytes", ctypes.c_double), ("lattice_updates", ctypes.c_double),
+                ("busy_seconds", ctypes.c_double), ("clock", ctypes.c_double)]
+
+
+SOLVE_STATUS = {0: "converged", 1: "max_steps", 2: "plateau", 3: "diverged", 4: "rejected",
+                5: "cancelled", 6: "error"}
+
+
+class Server:
+    """Continuous-batching solve server (``clbm_server``)."""
+
+    def __init__(self, dtype="f16s", hbm_budget_bytes=150e9, max_active=64, check_interval=100):
+        L = lib()
+        if not hasattr(L, "_server_ready"):
+            S = ctypes.c_void_p
+            L.clbm_server_create.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_int, ctypes.POINTER(S)]
+            L.clbm_server_submit.argtypes = [S, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_int64)]
+            L.clbm_server_wait.argtypes = [S, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(Result)]
+            L.clbm_server_results.argtypes = [S, ctypes.POINTER(Result), ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_int)]
+            L.clbm_server_fields.argtypes = [S, ctypes.c_int64, _D, _D, _D]
+            L.clbm_server_release.argtypes = [S, ctypes.c_int64]
+            L.clbm_server_info.argtypes = [S, ctypes.POINTER(ServerStats)]
+            L.clbm_server_destroy.argtypes = [S]
+            L.clbm_server_last_error.argtypes = [S]
+            L.clbm_server_last_error.restype = ctypes.c_char_p
+            for n in ("clbm_server_create", "clbm_server_submit", "clbm_server_wait",
+                      "clbm_server_results", "clbm_server_fields", "clbm_server_release",
+                      "clbm_server_info", "clbm_server_destroy"):
+                getattr(L, n).restype = ctypes.c_int
+            L._server_ready = True
+        self._s = ctypes.c_void_p()
+        code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        rc = L.clbm_server_create(code, float(hbm_budget_bytes), int(max_active),
+                                  int(check_interval), ctypes.byref(self._s))
+        if rc != OK:
+            msg = L.clbm_last_error(None)
+            raise CLBMError(rc, msg.decode() if msg else "")
+        self.shapes = {}
+
+    def _scheck(self, rc):
+        if rc != OK:
+            msg = lib().clbm_server_last_error(self._s)
+            raise CLBMError(rc, msg.decode() if msg else "")
+
+    def submit(self, nx, ny, nz, face, K, n, U_lid=None, body_force=None, tol=1e-7,
+               max_steps=0, plateau_checks=0, keep_fields=False, rho0=1.0, nu_min=0.0,
+               nu_max=0.0) -> int:
+        r = Request()
+        r.dom.nx, r.dom.ny, r.dom.nz = int(nx), int(ny), int(nz)
+        for i, f in enumerate(face):
+            r.dom.face[i] = int(f)
+        r.dom.rho0, r.dom.nu_min, r.dom.nu_max = float(rho0), float(nu_min), float(nu_max)
+        r.K, r.n = float(K), float(n)
+        for i in range(3):
+            r.U_lid[i] = float(U_lid[i]) if U_lid is not None else 0.0
+            r.body_force[i] = float(body_force[i]) if body_force is not None else 0.0
+        r.tol, r.max_steps = float(tol), int(max_steps)
+        r.plateau_checks, r.keep_fields = int(plateau_checks), int(bool(keep_fields))
+        rid = ctypes.c_int64()
+        self._scheck(lib().clbm_server_submit(self._s, ctypes.byref(r), ctypes.byref(rid)))
+        self.shapes[rid.value] = (int(nz), int(ny), int(nx))
+        return rid.value
+
+    def wait(self, rid: int, timeout: float = -1.0) -> dict:
+        res = Result()
+        self._scheck(lib().clbm_server_wait(self._s, int(rid), float(timeout), ctypes.byref(res)))
+        return res.as_dict()
+
+    def results(self, max_n: int = 4096) -> list:
+        arr = (Result * max_n)()
+        n = ctypes.c_int()
+        self._scheck(lib().clbm_server_results(self._s, arr, max_n, ctypes.byref(n)))
+        return [arr[i].as_dict() for i in range(n.value)]
+
+    def fields(self, rid: int):
+        shape = self.shapes[rid]
+        rho, u, gd = np.empty(shape), np.empty((3,) + shape), np.empty(shape)
+        self._scheck(lib().clbm_server_fields(self._s, int(rid), _dp(rho), _dp(u), _dp(gd)))
+        return rho, u, gd
+
+    def release(self, rid: int) -> None:
+        self._scheck(lib().clbm_server_release(self._s, int(rid)))
+
+    def info(self) -> dict:
+        st = ServerStats()
+        self._scheck(lib().clbm_server_info(self._s, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_s", None):
+            lib().clbm_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
