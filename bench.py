@@ -301,6 +301,12 @@ def run_ours(args):
     h2d = f0.nbytes / e2e_steps
     d2h = (rho.nbytes + u.nbytes + gd.nbytes) / e2e_steps
 
+    batch = serving = None
+    if not args.no_extra:
+        barrier()
+        batch = _batch_bench(clbm, torch, wl, args.batch_steps, peak)
+        serving = _serving_bench(clbm, wl, args.serve_requests, args.serve_seq)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = _cpu_baseline()
@@ -324,6 +330,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h,
                     "what": f"create + set_state from host + {e2e_steps} steps + fields to host, "
                             "one 128^3 n=0.5 cavity, FP32 storage, wall clock"},
+            "batch": batch,
+            "serving": serving,
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -333,6 +341,102 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _batch_bench(clbm, torch, wl, steps, peak):
+    """64 seeded cavities of uneven size in one batch (FP32), against the same
+    lattices stepped one launch at a time."""
+    probs = wl.batch_cavities(count=64, seed=0)
+    lats = [clbm.Lattice(**p.kwargs(), dtype="f32") for p in probs]
+    N = sum(p.N for p in probs)
+    with clbm.Batch("f32", capacity=len(lats), check_interval=100) as b:
+        for lt in lats:
+            b.add(lt)
+        tuned = b.autotune(4)
+        b.step(200)                          # warm-up: graph capture and caches
+        b.sync()
+        t0 = time.perf_counter()
+        b.step(steps)
+        b.sync()
+        dt = time.perf_counter() - t0
+        diverged = sum(1 for s in range(len(lats)) if b.stats(s)["diverged"])
+    mlups = N * steps / dt / 1e6
+    # the same lattices, one launch per lattice per step
+    for lt in lats:
+        lt.sync()
+    n_alone = max(10, steps // 10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_alone):
+        for lt in lats:
+            lt.step(1)
+    for lt in lats:
+        lt.sync()
+    dt_alone = time.perf_counter() - t0
+    for lt in lats:
+        lt.close()
+    gbs = 152 * N * steps / dt / 1e9
+    return {"workload": "64 cavities, L~U{32..96}, Re~U[50,500], n~U[0.4,1.6], U=0.05, FP32, seed 0",
+            "nodes": N, "steps": steps, "MLUPS": mlups, "GB/s": gbs, "frac_of_hbm": gbs / peak,
+            "launch": tuned, "diverged_lattices": diverged,
+            "separate_launches_MLUPS": N * n_alone / dt_alone / 1e6,
+            "timing": "host wall clock around graph-captured batch steps, synchronised"}
+
+
+def _serving_bench(clbm, wl, n_req, seq_req):
+    """Poisson trace through the continuous-batching server (FP16S), and the
+    first requests solved one at a time by the plain FP64 solver."""
+    trace = wl.serving_trace(count=n_req, seed=0, rate=20.0, cavity_L=(16, 48),
+                             channel_H=(16, 64), Re_range=(50.0, 400.0))
+    tol, cap, plateau = 1e-7, 200_000, 20
+    with clbm.Server("f16s", hbm_budget_bytes=150e9, max_active=64, check_interval=100) as srv:
+        t0 = time.perf_counter()
+        ids = []
+        for r in trace:
+            delay = t0 + r.arrival - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(**r.problem.kwargs(), tol=tol, max_steps=cap,
+                                  plateau_checks=plateau))
+        res = [srv.wait(i) for i in ids]
+        info = srv.info()
+    lat = sorted(r["t_done"] - r["t_submit"] for r in res)
+    span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+    status = {}
+    for r in res:
+        k = clbm.SOLVE_STATUS[r["status"]]
+        status[k] = status.get(k, 0) + 1
+    # sequential FP64 baseline on the first requests
+    t0 = time.perf_counter()
+    seq_steps = []
+    for r in trace[:seq_req]:
+        with clbm.Lattice(**r.problem.kwargs(), dtype="f64", check_interval=100) as lt:
+            best, since, steps = float("inf"), 0, 0
+            while steps < cap:
+                lt.step(100)
+                steps += 100
+                R, rc = lt.residual()
+                if rc != 0 or R <= tol:
+                    break
+                if R < 0.9 * best:
+                    best, since = R, 0
+                elif R == R and R != float("inf"):
+                    since += 1
+                if since >= plateau:
+                    break
+            seq_steps.append(steps)
+    seq_dt = time.perf_counter() - t0
+    q = lambda p: lat[min(len(lat) - 1, int(round(p * (len(lat) - 1))))]
+    return {"workload": f"{n_req} requests, Poisson 20/s (seed 0), half cavities L~U{{16..48}}, "
+                        "half channels 8xU{16..64}x8, Re~U[50,400], n~U[0.4,1.6], FP16S, "
+                        f"tol {tol}, cap {cap} steps, plateau {plateau} checks",
+            "solves_per_s": len(res) / span, "p50_latency_s": q(0.5), "p99_latency_s": q(0.99),
+            "makespan_s": span, "status": status,
+            "mean_steps": sum(r["steps"] for r in res) / len(res),
+            "server_MLUPS": info["lattice_updates"] / max(info["busy_seconds"], 1e-9) / 1e6,
+            "sequential_f64_solves_per_s": seq_req / seq_dt,
+            "sequential_f64_sample": f"first {seq_req} requests one at a time, plain FP64 "
+                                     f"handles, mean {sum(seq_steps) / len(seq_steps):.0f} steps"}
 
 
 def run_profile(args):
@@ -372,6 +476,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--forms", nargs="*", default=None)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched and serving measurements")
+    ap.add_argument("--batch-steps", type=int, default=500)
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-seq", type=int, default=4)
     ap.add_argument("--launch", type=int, nargs=3, default=None,
                     metavar=("BX", "BY", "NPT"), help="profiling case: fixed launch shape")
     ap.add_argument("--profile", nargs="?", const="f32", default=None,
