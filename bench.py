@@ -439,6 +439,33 @@ def _serving_bench(clbm, wl, n_req, seq_req):
                                      f"handles, mean {sum(seq_steps) / len(seq_steps):.0f} steps"}
 
 
+def run_profile_batch(args):
+    """The batch profiling case: the 64 seeded cavities in one FP32 batch."""
+    import torch
+    from paper_1908_05396_gb300 import build, workloads as wl
+    build.build()
+    from paper_1908_05396_gb300 import clbm
+    probs = wl.batch_cavities(count=64, seed=0)
+    lats = [clbm.Lattice(**p.kwargs(), dtype="f32") for p in probs]
+    with clbm.Batch("f32", capacity=len(lats), check_interval=100) as b:
+        for lt in lats:
+            b.add(lt)
+        if args.launch:
+            b.set_launch(args.launch[0], args.launch[1], args.launch[2], args.batch_bps)
+        b.step(args.warmup)
+        b.sync()
+        t0 = time.perf_counter()
+        b.step(args.steps)
+        b.sync()
+        dt = time.perf_counter() - t0
+    N = sum(p.N for p in probs)
+    print(json.dumps({"case": "batch of 64 cavities f32", "steps": args.steps,
+                      "MLUPS": N * args.steps / dt / 1e6}))
+    for lt in lats:
+        lt.close()
+    return 0
+
+
 def run_profile(args):
     """The profiling case: steps of one 128^3 cavity (n = 0.5) in one form."""
     import torch
@@ -481,6 +508,10 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-seq", type=int, default=4)
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="time only the batch of 64 cavities (profiling case)")
+    ap.add_argument("--batch-bps", type=int, default=4,
+                    help="profiling case: blocks per SM of the batch (negative: capped)")
     ap.add_argument("--launch", type=int, nargs=3, default=None,
                     metavar=("BX", "BY", "NPT"), help="profiling case: fixed launch shape")
     ap.add_argument("--profile", nargs="?", const="f32", default=None,
@@ -492,6 +523,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_batch:
+        return run_profile_batch(args)
     if args.profile:
         return run_profile(args)
     return run_ours(args)

@@ -187,10 +187,12 @@ int clbm_batch_step(clbm_batch b, int64_t nsteps);
 int clbm_batch_stats(clbm_batch b, int slot, double* residual, double* mass, int* diverged,
                      int64_t* steps);
 /* Launch shape: thread block (multiple of 32 threads, <= 256), planes per
- * tile zc >= 1, resident blocks per SM of the persistent grid. */
+ * tile zc >= 1, resident blocks per SM of the persistent grid (negative:
+ * the same count with the register-capped kernel variant). */
 int clbm_batch_set_launch(clbm_batch b, int block_x, int block_y, int zc, int blocks_per_sm);
-/* Time block shapes x zc x blocks-per-SM on the attached lattices (states
- * saved and restored) and keep the fastest. */
+/* Time block shapes x zc x blocks-per-SM x register cap on the attached
+ * lattices (states saved and restored) and keep the fastest; *blocks_per_sm
+ * is negative when the capped variant won. */
 int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int* zc,
                         int* blocks_per_sm, double* us_per_step);
 int clbm_batch_sync(clbm_batch b);

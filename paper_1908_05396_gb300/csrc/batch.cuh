@@ -1,13 +1,14 @@
 // batch.cuh -- one persistent launch that steps many lattices of uneven size.
 //
-// Every lattice is cut into tiles of (block_x x block_y) nodes times a chunk
-// of zc planes.  A device table maps each tile to its lattice, and each
-// lattice has a descriptor (buffers, geometry, collision constants) in device
-// memory.  A persistent grid of blocks strides over the tiles; a block
-// computes the per-direction offsets of its lattice once per tile and reuses
-// them for every plane of the chunk.  Parameters live in device memory, so a
-// CUDA graph captured once stays valid when lattices join or leave: only the
-// tables change.
+// Every lattice is cut into tiles of (block_x x block_y) nodes of one plane.
+// A device table maps each tile to its lattice, and each lattice has a
+// descriptor (buffers, geometry, collision constants) in a __constant__ table
+// of the translation unit.  A persistent grid of blocks strides over the
+// tiles.  Lattices with a body force come last in the tile table and are
+// stepped by a second launch compiled with the force path, so neither kernel
+// carries the registers of both paths.  Parameters live in device memory, so
+// a CUDA graph captured once stays valid when lattices join or leave: only
+// the tables change.
 #pragma once
 
 #include "kernels.cuh"
@@ -28,30 +29,35 @@ struct LatDesc {
 };
 
 // One node of the batched step: same pull, boundaries and collision as
-// step_kernel, with addresses from base + per-direction offset.
+// step_kernel.  Source offsets are formed from compile-time direction
+// constants right before each load, so no per-direction table is held in
+// registers.
 template <typename S, typename R, bool FORCE>
 __device__ __forceinline__ void batch_node(const LatDesc<R>& L, const S* __restrict__ src,
-                                           S* __restrict__ dst, const int (&off)[Q],
-                                           int x, int y, int z, NodeOut<R>& o) {
-  const int i = z * L.plane + y * L.pitch + x;
+                                           S* __restrict__ dst, int x, int y, int z,
+                                           NodeOut<R>& o) {
+  const int qs = int(L.qstride), plane = L.plane, pitch = L.pitch;
+  const int i = z * plane + y * pitch + x;
   R d[Q];
   if (y > 0 && y < L.ny - 1 && z > 0 && z < L.nz - 1) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) d[q] = Codec<S, R>::dec(src[off[q] + i], R(1));
+    for (int q = 0; q < Q; ++q)
+      d[q] = Codec<S, R>::dec(src[q * qs + i - (cz(q) * plane + cy(q) * pitch + cx(q))], R(1));
     if (x == 0 || x == L.nx - 1) {
       const int kl = L.facebits & 3, kr = (L.facebits >> 2) & 3;
 #pragma unroll
       for (int q = 1; q < Q; ++q) {
+        const int j = q * qs + i - (cz(q) * plane + cy(q) * pitch + cx(q));
         if (cx(q) == 1 && x == 0) {
           d[q] = kl == BC_PERIODIC
-                     ? Codec<S, R>::dec(src[off[q] + i + L.nx], R(1))
-                     : Codec<S, R>::dec(src[opp(q) * L.qstride + i], R(1)) +
+                     ? Codec<S, R>::dec(src[j + L.nx], R(1))
+                     : Codec<S, R>::dec(src[opp(q) * qs + i], R(1)) +
                            (kl == BC_LID ? L.lidc[q] : R(0));
         }
         if (cx(q) == -1 && x == L.nx - 1) {
           d[q] = kr == BC_PERIODIC
-                     ? Codec<S, R>::dec(src[off[q] + i - L.nx], R(1))
-                     : Codec<S, R>::dec(src[opp(q) * L.qstride + i], R(1)) +
+                     ? Codec<S, R>::dec(src[j - L.nx], R(1))
+                     : Codec<S, R>::dec(src[opp(q) * qs + i], R(1)) +
                            (kr == BC_LID ? L.lidc[q] : R(0));
         }
       }
@@ -59,64 +65,58 @@ __device__ __forceinline__ void batch_node(const LatDesc<R>& L, const S* __restr
   } else {
 #pragma unroll
     for (int q = 0; q < Q; ++q)
-      d[q] = pull_general<S, R>(src, L.qstride, L.nx, L.ny, L.nz, L.pitch, L.plane, L.facebits,
-                                q, x, y, z, i, L.lidc[q]);
+      d[q] = pull_general<S, R>(src, L.qstride, L.nx, L.ny, L.nz, pitch, plane, L.facebits, q,
+                                x, y, z, i, L.lidc[q]);
   }
   collide<R, FORCE>(L.C, d, o);
 #pragma unroll
-  for (int q = 0; q < Q; ++q) dst[q * L.qstride + i] = Codec<S, R>::enc(d[q], R(1));
+  for (int q = 0; q < Q; ++q) dst[q * qs + i] = Codec<S, R>::enc(d[q], R(1));
 }
 
-template <typename S, typename R, bool CHECK>
-__global__ void __launch_bounds__(256) batch_step_kernel(const LatDesc<R>* __restrict__ lats,
-                                                         const int* __restrict__ owner,
-                                                         BatchHeader* hdr, int parity,
-                                                         double* acc) {
-  const int ntiles = hdr->ntiles;
+// tile word: x tile (8 bits) | y tile (12 bits) | z chunk (12 bits)
+__host__ __device__ __forceinline__ unsigned tile_word(int tx, int ty, int tz) {
+  return unsigned(tx) | (unsigned(ty) << 8) | (unsigned(tz) << 20);
+}
+
+// The tile loop of the batched step.  get(li) returns lattice li's
+// descriptor from the translation unit's __constant__ table, so ptxas can
+// reload its fields where it needs them instead of holding them in registers.
+template <typename S, typename R, bool CHECK, bool FORCE, typename Get>
+__device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ owner,
+                                            const unsigned* __restrict__ coord,
+                                            BatchHeader* hdr, int parity, double* acc) {
+  // tiles [0, ntiles0) belong to lattices without force, [ntiles0, ntiles) with
+  const int t0 = FORCE ? hdr->ntiles0 : 0;
+  const int t1 = FORCE ? hdr->ntiles : hdr->ntiles0;
   const int nlat = hdr->nlat;
-  const int zc = hdr->zc;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (int t = t0 + int(blockIdx.x); t < t1; t += gridDim.x) {
     const int li = owner[t];
+    const unsigned w = coord[t];
+    const int tx = int(w & 0xffu), ty = int((w >> 8) & 0xfffu), tz = int(w >> 20);
     // Self-check of the tables before any access through them.
-    bool ok = li >= 0 && li < nlat && zc >= 1;
-    const LatDesc<R>& L = lats[ok ? li : 0];
-    if (ok) {
-      const int ntl = L.tiles_x * L.tiles_y * ((L.nz + zc - 1) / zc);
-      ok = L.buf[0] != nullptr && L.buf[1] != nullptr && L.nx >= 1 && L.ny >= 1 && L.nz >= 1 &&
-           L.tiles_x >= 1 && L.tiles_y >= 1 && t >= L.tile_begin && t < L.tile_begin + ntl &&
-           L.tiles_x * int(blockDim.x) >= L.nx && L.tiles_y * int(blockDim.y) >= L.ny &&
-           L.pitch >= L.nx && L.plane == L.pitch * L.ny && L.qstride >= int64_t(L.plane) * L.nz;
-    }
+    bool ok = li >= 0 && li < nlat;
+    const LatDesc<R>& L = get(ok ? li : 0);
+    if (ok)
+      ok = L.buf[0] != nullptr && L.buf[1] != nullptr && tx < L.tiles_x && ty < L.tiles_y &&
+           tz < L.nz && L.pitch >= L.nx && L.plane == L.pitch * L.ny &&
+           L.qstride >= int64_t(L.plane) * L.nz && 19 * L.qstride < (int64_t(1) << 31) &&
+           (L.C.has_force != 0) == FORCE;
     if (!ok) {  // block-uniform: skip the tile, report it
       if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(&hdr->err, 1);
       continue;
     }
-    const int local = t - L.tile_begin;
-    const int tx = local % L.tiles_x;
-    const int rest = local / L.tiles_x;
-    const int ty = rest % L.tiles_y;
-    const int z0 = (rest / L.tiles_y) * zc;
     const int x = tx * blockDim.x + threadIdx.x;
     const int y = ty * blockDim.y + threadIdx.y;
+    const int z = tz;
     const S* src = static_cast<const S*>(L.buf[parity]);
     S* dst = static_cast<S*>(const_cast<void*>(L.buf[parity ^ 1]));
-    // element offset of the upwind source of direction q (19 * qstride < 2^31
-    // is required of batched lattices)
-    int off[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q)
-      off[q] = q * int(L.qstride) - (cz(q) * L.plane + cy(q) * L.pitch + cx(q));
     const bool active = x < L.nx && y < L.ny;
-    const int z1 = min(z0 + zc, L.nz);
     double du2 = 0.0, uu = 0.0, dr = 0.0;
     int bad = 0;
     if (active) {
-      for (int z = z0; z < z1; ++z) {
+      {
         NodeOut<R> o;
-        if (L.C.has_force)
-          batch_node<S, R, true>(L, src, dst, off, x, y, z, o);
-        else
-          batch_node<S, R, false>(L, src, dst, off, x, y, z, o);
+        batch_node<S, R, FORCE>(L, src, dst, x, y, z, o);
         if (CHECK) {
           R* up = static_cast<R*>(L.uprev);
           const int64_t nst = int64_t(L.plane) * L.nz;
@@ -149,15 +149,9 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const LatDesc<R>* __res
   }
 }
 
-template <typename S, typename R>
-cudaError_t launch_batch_t(const void* lats, const int* owner, const void* hdr, int parity,
-                           bool check, double* acc, dim3 block, int grid, cudaStream_t st) {
-  const LatDesc<R>* L = static_cast<const LatDesc<R>*>(lats);
-  BatchHeader* H = static_cast<BatchHeader*>(const_cast<void*>(hdr));
-  if (check) batch_step_kernel<S, R, true><<<grid, block, 0, st>>>(L, owner, H, parity, acc);
-  else batch_step_kernel<S, R, false><<<grid, block, 0, st>>>(L, owner, H, parity, acc);
-  return cudaGetLastError();
-}
+// Bytes of __constant__ memory given to the descriptor table of one storage
+// form; batches reserve disjoint ranges of it.
+constexpr int BATCH_CONST_BYTES = 60 * 1024;
 
 // Host-side fill of one descriptor (constants converted once, in double).
 template <typename R>
@@ -189,14 +183,50 @@ void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur,
 
 #define CLBM_DEFINE_BATCH(SUFFIX, S, R)                                                        \
   namespace clbm {                                                                             \
-  cudaError_t launch_batch_##SUFFIX(const void* lats, const int* owner, const void* hdr,       \
-                                    int parity, bool check, double* acc, dim3 block, int grid, \
-                                    cudaStream_t st) {                                         \
-    return launch_batch_t<S, R>(lats, owner, hdr, parity, check, acc, block, grid, st);        \
+  __constant__ LatDesc<R> c_lat_##SUFFIX[BATCH_CONST_BYTES / sizeof(LatDesc<R>)];              \
+  template <bool CHECK, bool CAP, bool FORCE>                                                  \
+  __global__ void __launch_bounds__(256, CAP ? 4 : 1)                                          \
+      batch_kernel_##SUFFIX(int base, const int* __restrict__ owner,                           \
+                            const unsigned* __restrict__ coord, BatchHeader* hdr, int parity,  \
+                            double* acc) {                                                     \
+    batch_tiles<S, R, CHECK, FORCE>(                                                           \
+        [base](int li) -> const LatDesc<R>& { return c_lat_##SUFFIX[base + li]; }, owner,      \
+        coord, hdr, parity, acc);                                                              \
+  }                                                                                            \
+  cudaError_t launch_batch_##SUFFIX(int base, const int* owner, const unsigned* coord,         \
+                                    const void* hdr, int parity, bool check, double* acc,      \
+                                    dim3 block, int grid, cudaStream_t st) {                   \
+    BatchHeader* H = static_cast<BatchHeader*>(const_cast<void*>(hdr));                        \
+    const bool cap = grid < 0;                                                                 \
+    if (cap) grid = -grid;                                                                     \
+    /* tiles without force, then tiles with force (an empty range exits at once) */           \
+    if (check) {                                                                               \
+      if (cap) {                                                                               \
+        batch_kernel_##SUFFIX<true, true, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
+        batch_kernel_##SUFFIX<true, true, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
+      } else {                                                                                 \
+        batch_kernel_##SUFFIX<true, false, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
+        batch_kernel_##SUFFIX<true, false, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
+      }                                                                                        \
+    } else {                                                                                   \
+      if (cap) {                                                                               \
+        batch_kernel_##SUFFIX<false, true, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
+        batch_kernel_##SUFFIX<false, true, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
+      } else {                                                                                 \
+        batch_kernel_##SUFFIX<false, false, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
+        batch_kernel_##SUFFIX<false, false, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
+      }                                                                                        \
+    }                                                                                          \
+    return cudaGetLastError();                                                                 \
   }                                                                                            \
   size_t desc_size_##SUFFIX() { return sizeof(LatDesc<R>); }                                    \
+  int desc_capacity_##SUFFIX() { return int(BATCH_CONST_BYTES / sizeof(LatDesc<R>)); }         \
   void fill_desc_##SUFFIX(void* out, const Geom& g, const PhysParams& P, const void* cur,        \
                           const void* other, void* uprev, int tx, int ty, int tb, int slot) {  \
     fill_desc_t<R>(out, g, P, cur, other, uprev, tx, ty, tb, slot);                            \
+  }                                                                                            \
+  cudaError_t upload_desc_##SUFFIX(const void* host, int base, int n) {                        \
+    return cudaMemcpyToSymbol(c_lat_##SUFFIX, host, size_t(n) * sizeof(LatDesc<R>),            \
+                              size_t(base) * sizeof(LatDesc<R>), cudaMemcpyHostToDevice);      \
   }                                                                                            \
   }

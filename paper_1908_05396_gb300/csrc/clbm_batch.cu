@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
+#include <utility>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -34,20 +36,24 @@ struct clbm_batch_ctx {
   std::vector<int64_t> slot_checks;   // checks run since the lattice joined
   std::vector<int64_t> slot_joined;   // batch step at which it joined
   size_t desc_bytes = 0;
-  void* d_desc = nullptr;             // capacity descriptors
+  int desc_base = -1;                 // first entry of this batch in the constant table
+  void* d_desc = nullptr;             // small device allocation marking a live batch
   int* d_owner = nullptr;             // tile -> lattice index
+  unsigned* d_coord = nullptr;        // tile -> packed tile coordinates
   int owner_cap = 0;
   BatchHeader* d_hdr = nullptr;
   double* d_acc = nullptr;            // capacity x 4
   double* h_acc = nullptr;            // pinned copy
   void* h_stage = nullptr;            // pinned staging of descriptors
   std::vector<int> h_owner;
+  std::vector<unsigned> h_coord;
   int parity = 0;                     // steps since the tables were written, mod 2
   int64_t steps = 0;
   bool dirty = true;
   dim3 block{32, 4, 1};
   int zc = 4;
   int blocks_per_sm = 4;
+  bool cap = false;                   // register-capped kernel variant
   int sms = 1;
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t check_done = nullptr;
@@ -74,6 +80,45 @@ size_t desc_size(clbm_dtype t) {
   return t == CLBM_F64 ? desc_size_f64() : t == CLBM_F32 ? desc_size_f32() : desc_size_f16();
 }
 
+// Ranges of the per-form __constant__ descriptor tables held by live batches.
+std::mutex g_table_mu;
+std::vector<std::pair<int, int>> g_table_used[3];  // (base, count) per dtype
+
+int table_capacity(clbm_dtype t) {
+  return t == CLBM_F64 ? desc_capacity_f64() : t == CLBM_F32 ? desc_capacity_f32()
+                                                             : desc_capacity_f16();
+}
+
+int table_reserve(clbm_dtype t, int n) {
+  std::lock_guard<std::mutex> lk(g_table_mu);
+  auto& used = g_table_used[int(t)];
+  std::sort(used.begin(), used.end());
+  int base = 0;
+  for (auto& r : used) {
+    if (base + n <= r.first) break;
+    base = std::max(base, r.first + r.second);
+  }
+  if (base + n > table_capacity(t)) return -1;
+  used.emplace_back(base, n);
+  return base;
+}
+
+void table_release(clbm_dtype t, int base) {
+  std::lock_guard<std::mutex> lk(g_table_mu);
+  auto& used = g_table_used[int(t)];
+  for (size_t i = 0; i < used.size(); ++i)
+    if (used[i].first == base) {
+      used.erase(used.begin() + long(i));
+      return;
+    }
+}
+
+cudaError_t upload_desc(clbm_dtype t, const void* host, int base, int n) {
+  return t == CLBM_F64 ? upload_desc_f64(host, base, n)
+         : t == CLBM_F32 ? upload_desc_f32(host, base, n)
+                         : upload_desc_f16(host, base, n);
+}
+
 void fill_desc(clbm_dtype t, void* out, const clbm_ctx* h, int tx, int ty, int tb, int slot) {
   const void* cur = h->buf[h->cur];
   const void* other = h->buf[1 - h->cur];
@@ -83,17 +128,17 @@ void fill_desc(clbm_dtype t, void* out, const clbm_ctx* h, int tx, int ty, int t
 }
 
 cudaError_t launch(clbm_batch_ctx* b, bool check) {
-  const int grid = b->blocks_per_sm * b->sms;
+  const int grid = b->blocks_per_sm * b->sms * (b->cap ? -1 : 1);
   switch (b->dtype) {
     case CLBM_F64:
-      return launch_batch_f64(b->d_desc, b->d_owner, b->d_hdr, b->parity, check, b->d_acc,
-                              b->block, grid, b->stream);
+      return launch_batch_f64(b->desc_base, b->d_owner, b->d_coord, b->d_hdr, b->parity, check,
+                              b->d_acc, b->block, grid, b->stream);
     case CLBM_F32:
-      return launch_batch_f32(b->d_desc, b->d_owner, b->d_hdr, b->parity, check, b->d_acc,
-                              b->block, grid, b->stream);
+      return launch_batch_f32(b->desc_base, b->d_owner, b->d_coord, b->d_hdr, b->parity, check,
+                              b->d_acc, b->block, grid, b->stream);
     default:
-      return launch_batch_f16(b->d_desc, b->d_owner, b->d_hdr, b->parity, check, b->d_acc,
-                              b->block, grid, b->stream);
+      return launch_batch_f16(b->desc_base, b->d_owner, b->d_coord, b->d_hdr, b->parity, check,
+                              b->d_acc, b->block, grid, b->stream);
   }
 }
 
@@ -105,36 +150,51 @@ void drop_graph(clbm_batch_ctx* b) {
 // Rebuild and upload the tables from the attached lattices' current state.
 int upload(clbm_batch_ctx* b) {
   BCK(b, cudaStreamSynchronize(b->stream));  // staging buffers and tables are free
-  int ntiles = 0, nlat = 0;
-  std::vector<int> first;
+  int ntiles = 0, nlat = 0, ntiles0 = 0;
   b->h_owner.clear();
+  b->h_coord.clear();
   char* stage = static_cast<char*>(b->h_stage);
-  for (int s = 0; s < b->capacity; ++s) {
-    clbm_ctx* h = b->slots[s];
-    if (!h) continue;
-    const int tx = (h->g.nx + int(b->block.x) - 1) / int(b->block.x);
-    const int ty = (h->g.ny + int(b->block.y) - 1) / int(b->block.y);
-    const int tz = (h->g.nz + b->zc - 1) / b->zc;
-    fill_desc(b->dtype, stage + size_t(nlat) * b->desc_bytes, h, tx, ty, ntiles, s);
-    const int n = tx * ty * tz;
-    b->h_owner.insert(b->h_owner.end(), size_t(n), nlat);
-    ntiles += n;
-    ++nlat;
+  // lattices without body force first, then those with: two launches
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int s = 0; s < b->capacity; ++s) {
+      clbm_ctx* h = b->slots[s];
+      if (!h || (h->P.has_force != 0) != (pass == 1)) continue;
+      const int tx = (h->g.nx + int(b->block.x) - 1) / int(b->block.x);
+      const int ty = (h->g.ny + int(b->block.y) - 1) / int(b->block.y);
+      const int tz = h->g.nz;
+      if (tx > 255 || ty > 4095 || tz > 4095)
+        return bfail(b, CLBM_ERR_UNSUPPORTED, "lattice has too many tiles for the batch table");
+      fill_desc(b->dtype, stage + size_t(nlat) * b->desc_bytes, h, tx, ty, ntiles, s);
+      for (int kz = 0; kz < tz; ++kz)
+        for (int ky = 0; ky < ty; ++ky)
+          for (int kx = 0; kx < tx; ++kx) {
+            b->h_owner.push_back(nlat);
+            b->h_coord.push_back(unsigned(kx) | (unsigned(ky) << 8) | (unsigned(kz) << 20));
+          }
+      ntiles += tx * ty * tz;
+      ++nlat;
+    }
+    if (pass == 0) ntiles0 = ntiles;
   }
   if (ntiles > b->owner_cap) {
     if (b->d_owner) BCK(b, cudaFree(b->d_owner));
+    if (b->d_coord) BCK(b, cudaFree(b->d_coord));
     b->d_owner = nullptr;
+    b->d_coord = nullptr;
     const int cap = std::max(ntiles, 2 * b->owner_cap);
     BCK(b, cudaMalloc(reinterpret_cast<void**>(&b->d_owner), size_t(cap) * sizeof(int)));
+    BCK(b, cudaMalloc(reinterpret_cast<void**>(&b->d_coord), size_t(cap) * sizeof(unsigned)));
     b->owner_cap = cap;
     drop_graph(b);  // the graph holds the old table address
   }
-  BatchHeader hdr{nlat, ntiles, b->zc, 0};
-  if (nlat)
-    BCK(b, cudaMemcpy(b->d_desc, stage, size_t(nlat) * b->desc_bytes, cudaMemcpyHostToDevice));
-  if (ntiles)
+  BatchHeader hdr{nlat, ntiles, ntiles0, 0};
+  if (nlat) BCK(b, upload_desc(b->dtype, stage, b->desc_base, nlat));
+  if (ntiles) {
     BCK(b, cudaMemcpy(b->d_owner, b->h_owner.data(), size_t(ntiles) * sizeof(int),
                       cudaMemcpyHostToDevice));
+    BCK(b, cudaMemcpy(b->d_coord, b->h_coord.data(), size_t(ntiles) * sizeof(unsigned),
+                      cudaMemcpyHostToDevice));
+  }
   BCK(b, cudaMemcpy(b->d_hdr, &hdr, sizeof(hdr), cudaMemcpyHostToDevice));
   b->parity = 0;
   b->dirty = false;
@@ -231,7 +291,14 @@ int clbm_batch_create(clbm_dtype dtype, int capacity, int check_interval, void* 
   b->slots.assign(size_t(capacity), nullptr);
   b->slot_checks.assign(size_t(capacity), 0);
   b->slot_joined.assign(size_t(capacity), 0);
-  b->desc_bytes = desc_size(dtype);  // the kernel indexes the array with this stride
+  b->desc_bytes = desc_size(dtype);  // the kernel indexes the table with this stride
+  b->desc_base = table_reserve(dtype, capacity);
+  if (b->desc_base < 0) {
+    delete b;
+    return bfail(nullptr, CLBM_ERR_UNSUPPORTED,
+                 "the descriptor table of this storage form is full (" +
+                     std::to_string(table_capacity(dtype)) + " lattices over all live batches)");
+  }
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
   if (e == cudaSuccess) {
@@ -242,7 +309,7 @@ int clbm_batch_create(clbm_dtype dtype, int capacity, int check_interval, void* 
       b->own_stream = e == cudaSuccess;
     }
   }
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_desc, size_t(capacity) * b->desc_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_desc, 256);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_hdr), sizeof(BatchHeader));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&b->d_acc), size_t(capacity) * 4 * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&b->h_acc), size_t(capacity) * 4 * sizeof(double));
@@ -341,6 +408,8 @@ int clbm_batch_stats(clbm_batch b, int slot, double* residual, double* mass, int
 
 int clbm_batch_set_launch(clbm_batch b, int block_x, int block_y, int zc, int blocks_per_sm) {
   if (!valid(b)) return bfail(b, CLBM_ERR_ARG, "invalid batch");
+  const bool cap = blocks_per_sm < 0;
+  if (cap) blocks_per_sm = -blocks_per_sm;
   if (block_x < 1 || block_y < 1 || block_x * block_y > 256 || (block_x * block_y) % 32 ||
       zc < 1 || blocks_per_sm < 1 || blocks_per_sm > 32)
     return bfail(b, CLBM_ERR_ARG, "bad launch shape");
@@ -349,6 +418,7 @@ int clbm_batch_set_launch(clbm_batch b, int block_x, int block_y, int zc, int bl
   b->block = dim3(block_x, block_y, 1);
   b->zc = zc;
   b->blocks_per_sm = blocks_per_sm;
+  b->cap = cap;
   b->dirty = true;
   drop_graph(b);
   return CLBM_OK;
@@ -379,18 +449,22 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
   const dim3 block0 = b->block;
   const int zc0 = b->zc, bps0 = b->blocks_per_sm;
   const int shapes[][2] = {{32, 2}, {32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}};
-  const int zcs[] = {1, 2, 4, 8};
+  const int zcs[] = {1};
   const int bpss[] = {4, 6, 8};
+  const bool cap0 = b->cap;
   double best = 1e300;
   int bx = block0.x, by = block0.y, bz = zc0, bb = bps0;
+  bool bc = cap0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (err == cudaSuccess) err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  for (int capped = 0; capped <= 1; ++capped)
   for (auto& sh : shapes)
     for (int z : zcs)
       for (int bp : bpss) {
         if (err != cudaSuccess) break;
         if (sh[0] * sh[1] * bp > 2048) continue;   // at most 2048 threads per SM
+        b->cap = capped != 0;
         b->block = dim3(sh[0], sh[1], 1);
         b->zc = z;
         b->blocks_per_sm = bp;
@@ -415,6 +489,7 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
           by = sh[1];
           bz = z;
           bb = bp;
+          bc = capped != 0;
         }
       }
   if (e0) cudaEventDestroy(e0);
@@ -435,6 +510,7 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
   b->block = dim3(bx, by, 1);
   b->zc = bz;
   b->blocks_per_sm = bb;
+  b->cap = bc;
   b->dirty = true;
   drop_graph(b);
   cudaError_t e3 = cudaStreamSynchronize(b->stream);
@@ -444,7 +520,7 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
   if (block_x) *block_x = bx;
   if (block_y) *block_y = by;
   if (zc) *zc = bz;
-  if (blocks_per_sm) *blocks_per_sm = bb;
+  if (blocks_per_sm) *blocks_per_sm = bc ? -bb : bb;  // negative: register-capped variant
   if (us_per_step) *us_per_step = best;
   return CLBM_OK;
 }
@@ -464,7 +540,9 @@ int clbm_batch_destroy(clbm_batch b) {
     if (h) h->batch = nullptr;
   drop_graph(b);
   if (b->d_desc) cudaFree(b->d_desc);
+  if (b->desc_base >= 0) table_release(b->dtype, b->desc_base);
   if (b->d_owner) cudaFree(b->d_owner);
+  if (b->d_coord) cudaFree(b->d_coord);
   if (b->d_hdr) cudaFree(b->d_hdr);
   if (b->d_acc) cudaFree(b->d_acc);
   if (b->h_acc) cudaFreeHost(b->h_acc);

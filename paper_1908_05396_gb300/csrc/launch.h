@@ -64,15 +64,17 @@ void set_unbound_error(const char* msg);
 // Batched step (batch.cuh): descriptors are opaque bytes to the host code.
 struct BatchHeader {
   int nlat;
-  int ntiles;
-  int zc;   // planes per tile
-  int err;  // set by the kernel if a tile's descriptor fails its checks
+  int ntiles;   // all tiles
+  int ntiles0;  // tiles of lattices without body force (they come first)
+  int err;      // set by the kernel if a tile's descriptor fails its checks
 };
 #define CLBM_DECLARE_BATCH(SUFFIX)                                                              \
-  cudaError_t launch_batch_##SUFFIX(const void* lats, const int* owner, const void* hdr,        \
-                                    int parity, bool check, double* acc, dim3 block, int grid,  \
-                                    cudaStream_t st);                                           \
+  cudaError_t launch_batch_##SUFFIX(int base, const int* owner, const unsigned* coord,         \
+                                    const void* hdr, int parity, bool check, double* acc,       \
+                                    dim3 block, int grid, cudaStream_t st);                     \
   size_t desc_size_##SUFFIX();                                                                  \
+  int desc_capacity_##SUFFIX();                                                                 \
+  cudaError_t upload_desc_##SUFFIX(const void* host, int base, int n);                          \
   void fill_desc_##SUFFIX(void* out, const Geom& g, const PhysParams& P, const void* cur,       \
                           const void* other, void* uprev, int tx, int ty, int tb, int slot);
 CLBM_DECLARE_BATCH(f64)
