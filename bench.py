@@ -439,6 +439,75 @@ def _serving_bench(clbm, wl, n_req, seq_req):
                                      f"handles, mean {sum(seq_steps) / len(seq_steps):.0f} steps"}
 
 
+def _run_to_steady(clbm, prob, dtype, tol, max_steps, plateau=20, chunk=1000):
+    with clbm.Lattice(**prob.kwargs(), dtype=dtype, check_interval=100) as lat:
+        lat.autotune(5)
+        best, since, steps, R, status = float("inf"), 0, 0, float("inf"), "max_steps"
+        t0 = time.perf_counter()
+        while steps < max_steps:
+            lat.step(chunk)
+            steps += chunk
+            R, rc = lat.residual()
+            if rc != 0:
+                status = "diverged"
+                break
+            if R <= tol:
+                status = "converged"
+                break
+            if R < 0.9 * best:
+                best, since = R, 0
+            else:
+                since += 1
+            if since >= plateau:
+                status = "plateau"
+                break
+        dt = time.perf_counter() - t0
+        _, u, _ = lat.fields()
+    return u, {"steps": steps, "residual": R, "status": status, "seconds": dt}
+
+
+def run_precision(args):
+    """Velocity error of the FP32 and FP16-shifted forms against FP64: a 64^3
+    cavity (Re 100, n 0.8) at steady state, and the 256^3 Re 1000 n 0.8
+    cavity after a fixed number of steps (the FP64 form is ALU bound, and a
+    256^3 steady state needs ~1e6 steps)."""
+    import numpy as np
+    import torch  # noqa: F401  (CUDA context on the chosen device)
+    from paper_1908_05396_gb300 import build, workloads as wl
+    build.build()
+    from paper_1908_05396_gb300 import clbm
+    out = {"metric": "precision", "cases": []}
+    prob = wl.cavity(64, 100.0, 0.8)
+    res = {}
+    for dt in ("f64", "f32", "f16s", "f16r"):
+        res[dt] = _run_to_steady(clbm, prob, dt, 1e-8, 600_000)
+    n64 = float(np.linalg.norm(res["f64"][0]))
+    out["cases"].append({
+        "case": "cavity 64^3, Re 100, n 0.8, U 0.05, run to R <= 1e-8 (F16S: or plateau)",
+        "runs": {k: v[1] for k, v in res.items()},
+        "l2_vs_f64": {k: float(np.linalg.norm(res[k][0] - res["f64"][0])) / n64
+                      for k in ("f32", "f16s", "f16r")}})
+    prob = wl.cavity(256, 1000.0, 0.8)
+    fixed = {}
+    for dt in ("f64", "f32", "f16s", "f16r"):
+        with clbm.Lattice(**prob.kwargs(), dtype=dt) as lat:
+            lat.autotune(3)
+            t0 = time.perf_counter()
+            lat.step(args.precision_steps)
+            lat.sync()
+            sec = time.perf_counter() - t0
+            _, u, _ = lat.fields()
+        fixed[dt] = (u, sec)
+    n64 = float(np.linalg.norm(fixed["f64"][0]))
+    out["cases"].append({
+        "case": f"cavity 256^3, Re 1000, n 0.8, U 0.05, {args.precision_steps} steps from rest",
+        "seconds": {k: v[1] for k, v in fixed.items()},
+        "l2_vs_f64": {k: float(np.linalg.norm(fixed[k][0] - fixed["f64"][0])) / n64
+                      for k in ("f32", "f16s", "f16r")}})
+    print(json.dumps(out))
+    return 0
+
+
 def run_profile_batch(args):
     """The batch profiling case: the 64 seeded cavities in one FP32 batch."""
     import torch
@@ -508,6 +577,9 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-seq", type=int, default=4)
+    ap.add_argument("--precision", action="store_true",
+                    help="velocity error of the FP32 / F16S forms against FP64")
+    ap.add_argument("--precision-steps", type=int, default=2000)
     ap.add_argument("--profile-batch", action="store_true",
                     help="time only the batch of 64 cavities (profiling case)")
     ap.add_argument("--batch-bps", type=int, default=4,
@@ -525,6 +597,8 @@ def main():
         return run_reference(args)
     if args.profile_batch:
         return run_profile_batch(args)
+    if args.precision:
+        return run_precision(args)
     if args.profile:
         return run_profile(args)
     return run_ours(args)

@@ -57,8 +57,15 @@ extern "C" {
  *   CLBM_F32  : f - w rho0 stored in FP32, collision in FP32.
  *   CLBM_F16S : (f - w rho0) * 1024 stored in FP16 (round to nearest even),
  *               collision in FP32.
+ *   CLBM_F16R : (f - w [rho0 + drho + 3 (rho0 + drho)(e . u)]) * 1024 in
+ *               FP16, relative to the writing node's own (drho, u), which is
+ *               stored beside the populations as four FP16 values; collision
+ *               in FP32.  Removing the first-order equilibrium before
+ *               rounding keeps steady states close to FP64.  16 more bytes
+ *               per node update than F16S.  Not available to clbm_batch_* or
+ *               clbm_step_noalloc.
  * Residual and mass reductions accumulate in FP64 for every form. */
-typedef enum { CLBM_F64 = 0, CLBM_F32 = 1, CLBM_F16S = 2 } clbm_dtype;
+typedef enum { CLBM_F64 = 0, CLBM_F32 = 1, CLBM_F16S = 2, CLBM_F16R = 3 } clbm_dtype;
 
 /* Face kinds, for faces ordered (-x, +x, -y, +y, -z, +z).
  *   CLBM_PERIODIC : both faces of the pair must be periodic.

@@ -15,9 +15,9 @@ import numpy as np
 from . import build as _build
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
-F64, F32, F16S = 0, 1, 2
+F64, F32, F16S, F16R = 0, 1, 2, 3
 PERIODIC, WALL, LID = 0, 1, 2
-DTYPES = {"f64": F64, "f32": F32, "f16s": F16S}
+DTYPES = {"f64": F64, "f32": F32, "f16s": F16S, "f16r": F16R}
 
 _LOCK = threading.Lock()
 _LIB = None

@@ -278,6 +278,8 @@ int clbm_batch_create(clbm_dtype dtype, int capacity, int check_interval, void* 
                       clbm_batch* out) {
   if (!out) return bfail(nullptr, CLBM_ERR_ARG, "null output");
   *out = nullptr;
+  if (dtype == CLBM_F16R)
+    return bfail(nullptr, CLBM_ERR_UNSUPPORTED, "the batched step does not take the F16R form");
   if (dtype != CLBM_F64 && dtype != CLBM_F32 && dtype != CLBM_F16S)
     return bfail(nullptr, CLBM_ERR_ARG, "unknown dtype");
   if (capacity < 1 || capacity > (1 << 16)) return bfail(nullptr, CLBM_ERR_ARG, "capacity must be in [1, 65536]");

@@ -51,8 +51,11 @@ cudaError_t dispatch_step(clbm_ctx* h, bool check) {
   const void* src = h->buf[h->cur];
   void* dst = h->buf[1 - h->cur];
   switch (h->dtype) {
-    case CLBM_F64: return launch_step_f64(src, dst, h->g, h->P, cb, check, h->block, 1, h->stream);
+    case CLBM_F64: return launch_step_f64(src, dst, h->g, h->P, cb, check, h->block, h->npt & 4 ? 5 : 1, h->stream);
     case CLBM_F32: return launch_step_f32(src, dst, h->g, h->P, cb, check, h->block, h->npt, h->stream);
+    case CLBM_F16R:
+      return launch_step_f16r(src, dst, h->ref[h->cur], h->ref[1 - h->cur], h->g, h->P, cb, check,
+                              h->block, h->npt, h->stream);
     default: return launch_step_f16(src, dst, h->g, h->P, cb, check, h->block, h->npt, h->stream);
   }
 }
@@ -82,7 +85,7 @@ void fill_params(PhysParams& P, double K, double n, const double* F, double rho0
   P.nu_max = nu_max;
   P.ylo = std::log(3.0 * nu_min);
   P.yhi = std::log(3.0 * nu_max);
-  P.inv_scale = dtype == CLBM_F16S ? 1.0 / F16_SCALE : 1.0;
+  P.inv_scale = (dtype == CLBM_F16S || dtype == CLBM_F16R) ? 1.0 / F16_SCALE : 1.0;
 }
 
 int check_phys(double K, double n, double nu_min, double nu_max, std::string& why) {
@@ -107,7 +110,7 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
                 const double body_force[3], clbm_dtype dtype, clbm_handle* out) {
   if (!d || !out) return fail(nullptr, CLBM_ERR_ARG, "null domain or output pointer");
   *out = nullptr;
-  if (dtype != CLBM_F64 && dtype != CLBM_F32 && dtype != CLBM_F16S)
+  if (dtype != CLBM_F64 && dtype != CLBM_F32 && dtype != CLBM_F16S && dtype != CLBM_F16R)
     return fail(nullptr, CLBM_ERR_ARG, "unknown dtype");
   if (d->nx < 1 || d->ny < 1 || d->nz < 1)
     return fail(nullptr, CLBM_ERR_ARG, "lattice dimensions must be >= 1");
@@ -150,7 +153,7 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
   h->dom.nu_max = nu_max;
   if (h->dom.check_interval <= 0) h->dom.check_interval = 100;
   h->dtype = dtype;
-  h->elem = dtype == CLBM_F64 ? 8 : dtype == CLBM_F32 ? 4 : 2;
+  h->elem = dtype == CLBM_F64 ? 8 : dtype == CLBM_F32 ? 4 : 2;  // F16S, F16R: 2
   h->rsize = dtype == CLBM_F64 ? 8 : 4;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) {
@@ -191,6 +194,14 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
   for (int b = 0; b < 2; ++b) {
     e = cudaMalloc(&h->buf[b], pop_bytes);
     if (e != cudaSuccess) return cleanup(CLBM_ERR_OOM, "population buffer allocation failed");
+  }
+  if (dtype == CLBM_F16R) {
+    const size_t ref_bytes = (size_t(g.plane) * g.nz + 64) * 8;  // 4 halves per node, + slack
+    for (int b = 0; b < 2; ++b) {
+      e = cudaMalloc(&h->ref[b], ref_bytes);
+      if (e == cudaSuccess) e = cudaMemset(h->ref[b], 0, ref_bytes);
+      if (e != cudaSuccess) return cleanup(CLBM_ERR_OOM, "reference buffer allocation failed");
+    }
   }
   e = cudaMalloc(&h->uprev, 3 * size_t(g.plane) * g.nz * h->rsize);
   if (e != cudaSuccess) return cleanup(CLBM_ERR_OOM, "velocity buffer allocation failed");
@@ -250,6 +261,9 @@ static int fields_impl(clbm_handle h, double* rho, double* u, double* gd) {
   switch (h->dtype) {
     case CLBM_F64: e = launch_fields_f64(src, h->g, h->P, rho, u, gd, h->stream); break;
     case CLBM_F32: e = launch_fields_f32(src, h->g, h->P, rho, u, gd, h->stream); break;
+    case CLBM_F16R:
+      e = launch_fields_f16r(src, h->ref[h->cur], h->g, h->P, rho, u, gd, h->stream);
+      break;
     default: e = launch_fields_f16(src, h->g, h->P, rho, u, gd, h->stream); break;
   }
   CK(h, e);
@@ -330,6 +344,9 @@ static int state_io(clbm_handle h, double* out, const double* in) {
       switch (h->dtype) {
         case CLBM_F64: e = launch_import_f64(dev, h->g, h->g.rho0, isc, h->buf[h->cur], h->stream); break;
         case CLBM_F32: e = launch_import_f32(dev, h->g, h->g.rho0, isc, h->buf[h->cur], h->stream); break;
+        case CLBM_F16R:
+          e = launch_import_f16r(dev, h->g, h->g.rho0, h->buf[h->cur], h->ref[h->cur], h->stream);
+          break;
         default: e = launch_import_f16(dev, h->g, h->g.rho0, isc, h->buf[h->cur], h->stream); break;
       }
     }
@@ -337,6 +354,9 @@ static int state_io(clbm_handle h, double* out, const double* in) {
     switch (h->dtype) {
       case CLBM_F64: e = launch_export_f64(h->buf[h->cur], h->g, h->g.rho0, isc, dev, h->stream); break;
       case CLBM_F32: e = launch_export_f32(h->buf[h->cur], h->g, h->g.rho0, isc, dev, h->stream); break;
+      case CLBM_F16R:
+        e = launch_export_f16r(h->buf[h->cur], h->ref[h->cur], h->g, h->g.rho0, dev, h->stream);
+        break;
       default: e = launch_export_f16(h->buf[h->cur], h->g, h->g.rho0, isc, dev, h->stream); break;
     }
     if (e == cudaSuccess)
@@ -400,7 +420,7 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
   const int shapes[][2] = {{32, 1}, {32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2}, {64, 4},
                            {128, 1}, {128, 2}, {256, 1}};
   for (int capped = 0; capped <= 1; ++capped)
-    for (int np = 1; np <= (h->dtype == CLBM_F64 ? 1 : 2); ++np)
+    for (int np = 1; np <= ((h->dtype == CLBM_F64 || h->dtype == CLBM_F16R) ? 1 : 2); ++np)
       for (auto& sh : shapes) {
         if (sh[0] * sh[1] > (np == 2 ? 128 : 256)) continue;
         if (sh[0] > 32 && sh[0] > h->g.pitch) continue;
@@ -408,9 +428,13 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
       }
   // Save the state: tuning runs real steps.
   const size_t pop_bytes = size_t(NQ) * size_t(h->g.qstride) * h->elem;
+  const size_t ref_bytes = h->ref[0] ? (size_t(h->g.plane) * h->g.nz + 64) * 8 : 0;
   void* saved = nullptr;
-  CK(h, cudaMallocAsync(&saved, pop_bytes, h->stream));
+  CK(h, cudaMallocAsync(&saved, pop_bytes + ref_bytes, h->stream));
   CK(h, cudaMemcpyAsync(saved, h->buf[h->cur], pop_bytes, cudaMemcpyDeviceToDevice, h->stream));
+  if (ref_bytes)
+    CK(h, cudaMemcpyAsync(static_cast<char*>(saved) + pop_bytes, h->ref[h->cur], ref_bytes,
+                          cudaMemcpyDeviceToDevice, h->stream));
   const int cur0 = h->cur;
   cudaEvent_t e0, e1;
   CK(h, cudaEventCreate(&e0));
@@ -449,6 +473,9 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
   h->cur = cur0;
   cudaError_t e2 = cudaMemcpyAsync(h->buf[h->cur], saved, pop_bytes, cudaMemcpyDeviceToDevice,
                                    h->stream);
+  if (e2 == cudaSuccess && ref_bytes)
+    e2 = cudaMemcpyAsync(h->ref[h->cur], static_cast<char*>(saved) + pop_bytes, ref_bytes,
+                         cudaMemcpyDeviceToDevice, h->stream);
   cudaFreeAsync(saved, h->stream);
   if (err == cudaSuccess) err = e2;
   if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
@@ -479,7 +506,7 @@ int clbm_set_launch(clbm_handle h, int block_x, int block_y, int npt) {
       block_x * block_y % 32 != 0)
     return fail(h, CLBM_ERR_ARG, "block must have a multiple of 32 threads, at most 256 "
                                  "(128 with two nodes per thread)");
-  if (np == 2 && h->dtype == CLBM_F64)
+  if (np == 2 && (h->dtype == CLBM_F64 || h->dtype == CLBM_F16R))
     return fail(h, CLBM_ERR_UNSUPPORTED, "two nodes per thread needs FP32 math");
   h->block = dim3(block_x, block_y, 1);
   h->npt = npt;
@@ -491,8 +518,10 @@ int clbm_destroy(clbm_handle h) {
   if (h->batch) clbm_batch_detach(h->batch, h);
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
-  for (int b = 0; b < 2; ++b)
+  for (int b = 0; b < 2; ++b) {
     if (h->buf[b]) cudaFree(h->buf[b]);
+    if (h->ref[b]) cudaFree(h->ref[b]);
+  }
   if (h->uprev) cudaFree(h->uprev);
   if (h->acc) cudaFree(h->acc);
   if (h->host) cudaFreeHost(h->host);
@@ -511,7 +540,7 @@ int clbm_collide_nodes(clbm_dtype dtype, double K, double n, const double body_f
                        double rho0, double nu_min, double nu_max, const double* f_in,
                        double* f_out, double* rho, double* u, double* gamma_dot, int64_t M) {
   if (!f_in || !f_out || M <= 0) return fail(nullptr, CLBM_ERR_ARG, "bad node arrays");
-  if (dtype != CLBM_F64 && dtype != CLBM_F32 && dtype != CLBM_F16S)
+  if (dtype != CLBM_F64 && dtype != CLBM_F32 && dtype != CLBM_F16S && dtype != CLBM_F16R)
     return fail(nullptr, CLBM_ERR_ARG, "unknown dtype");
   rho0 = rho0 > 0 ? rho0 : 1.0;
   nu_min = nu_min > 0 ? nu_min : 5e-4;
@@ -534,6 +563,7 @@ int clbm_collide_nodes(clbm_dtype dtype, double K, double n, const double body_f
     switch (dtype) {
       case CLBM_F64: e = launch_collide_nodes_f64(P, din, dout, drho, du, dgd, M, 0); break;
       case CLBM_F32: e = launch_collide_nodes_f32(P, din, dout, drho, du, dgd, M, 0); break;
+      case CLBM_F16R: e = launch_collide_nodes_f16r(P, din, dout, drho, du, dgd, M, 0); break;
       default: e = launch_collide_nodes_f16(P, din, dout, drho, du, dgd, M, 0); break;
     }
   }

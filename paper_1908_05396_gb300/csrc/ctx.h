@@ -17,6 +17,7 @@ struct clbm_ctx {
   size_t elem = 8;       // bytes per stored population
   size_t rsize = 8;      // bytes per math-precision value
   void* buf[2] = {nullptr, nullptr};
+  void* ref[2] = {nullptr, nullptr};  // F16R: per-node reference moments, with buf
   int cur = 0;           // buffer holding the current state
   void* uprev = nullptr;
   double* acc = nullptr; // device: 3 doubles, then the int flag

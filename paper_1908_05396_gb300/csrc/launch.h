@@ -8,7 +8,7 @@ namespace clbm {
 
 enum { BC_PERIODIC = 0, BC_WALL = 1, BC_LID = 2 };
 constexpr int NQ = 19;  // D3Q19 directions
-enum { DT_F64 = 0, DT_F32 = 1, DT_F16S = 2 };
+enum { DT_F64 = 0, DT_F32 = 1, DT_F16S = 2, DT_F16R = 3 };
 
 // Power-of-two scale of the FP16 shifted storage: stored = (f - w rho0) * 1024.
 constexpr double F16_SCALE = 1024.0;
@@ -80,6 +80,22 @@ struct BatchHeader {
 CLBM_DECLARE_BATCH(f64)
 CLBM_DECLARE_BATCH(f32)
 CLBM_DECLARE_BATCH(f16)
+
+// F16R form (step_f16r.cu): FP16 populations relative to each node's stored
+// first-order equilibrium reference.
+cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, void* ref_dst,
+                             const Geom& g, const PhysParams& P, const CheckBufs& cb, bool check,
+                             dim3 block, int npt, cudaStream_t st);
+cudaError_t launch_fields_f16r(const void* src, const void* ref, const Geom& g,
+                               const PhysParams& P, double* rho, double* u, double* gd,
+                               cudaStream_t st);
+cudaError_t launch_export_f16r(const void* src, const void* ref, const Geom& g, double rho0,
+                               double* out, cudaStream_t st);
+cudaError_t launch_import_f16r(const double* in, const Geom& g, double rho0, void* dst, void* ref,
+                               cudaStream_t st);
+cudaError_t launch_collide_nodes_f16r(const PhysParams& P, const double* fin, double* fout,
+                                      double* rho, double* u, double* gd, int64_t M,
+                                      cudaStream_t st);
 
 CLBM_DECLARE_LAUNCHERS(f64)
 CLBM_DECLARE_LAUNCHERS(f32)

@@ -169,7 +169,8 @@ extern "C" int clbm_step_noalloc(const clbm_domain* d, double K, double n, const
     return noalloc_fail(CLBM_ERR_ARG, "null domain or buffer");
   if (src == dst) return noalloc_fail(CLBM_ERR_ARG, "src and dst must be different buffers");
   if (dtype != CLBM_F64 && dtype != CLBM_F32 && dtype != CLBM_F16S)
-    return noalloc_fail(CLBM_ERR_ARG, "unknown dtype");
+    return noalloc_fail(dtype == 3 ? CLBM_ERR_UNSUPPORTED : CLBM_ERR_ARG,
+                        dtype == 3 ? "the F16R form is not available here" : "unknown dtype");
   if (d->nx < 1 || d->ny < 1 || d->nz < 1)
     return noalloc_fail(CLBM_ERR_ARG, "lattice dimensions must be >= 1");
   bool has_lid = false;

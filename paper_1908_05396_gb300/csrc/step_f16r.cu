@@ -1,0 +1,381 @@
+// step_f16r.cu -- kernels of the F16R storage form: FP16 populations stored
+// relative to the writing node's first-order equilibrium.
+//
+// Each node keeps a reference (rho - rho0, u) of its last collision as four
+// FP16 values next to its populations, and stores
+//     s_q = fp16( 1024 * ( f~_q - w_q rho0 - r_q ) ),
+//     r_q = w_q [ drho + 3 (rho0 + drho) (e_q . u) ]        (reference values),
+// which removes the rest value and the first-order (velocity) part of the
+// equilibrium, the largest parts of f~, before FP16 rounding.  A reader
+// decodes with the reference of the node that wrote the value: the upwind
+// neighbour for a streamed value, itself for a bounced one.  Both sides use
+// the reference exactly as stored (rounded to FP16), so the encoding is
+// exactly invertible up to the FP16 rounding of the small remainder.
+// The reference arrays are double-buffered with the populations.
+#include "kernels.cuh"
+
+namespace clbm {
+namespace {
+
+struct Ref4 {
+  float dr, ux, uy, uz;
+};
+
+__device__ __forceinline__ Ref4 ref_load(const uint2* p) {
+  const uint2 v = *p;
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+  return {a.x, a.y, b.x, b.y};
+}
+
+// Round (drho, u) to FP16 for storage; r receives the rounded values.
+__device__ __forceinline__ uint2 ref_pack(float dr, float ux, float uy, float uz, Ref4& r) {
+  const __half2 a = __floats2half2_rn(dr, ux), b = __floats2half2_rn(uy, uz);
+  const float2 fa = __half22float2(a), fb = __half22float2(b);
+  r = {fa.x, fa.y, fb.x, fb.y};
+  uint2 v;
+  v.x = *reinterpret_cast<const unsigned*>(&a);
+  v.y = *reinterpret_cast<const unsigned*>(&b);
+  return v;
+}
+
+// First-order equilibrium deviation of direction q about the reference.
+__device__ __forceinline__ float ref_term(int q, const Ref4& r, float rho0) {
+  const float eu = float(cx(q)) * r.ux + float(cy(q)) * r.uy + float(cz(q)) * r.uz;
+  return wt<float>(q) * (r.dr + 3.0f * (rho0 + r.dr) * eu);
+}
+
+__device__ __forceinline__ float dec16(__half v) { return __half2float(v) * float(1.0 / F16_SCALE); }
+__device__ __forceinline__ __half enc16(float v) { return __float2half_rn(v * float(F16_SCALE)); }
+
+struct RefArgs {
+  const uint2* refq[Q];  // refq[q][i]: reference of the upwind neighbour of node i
+  const uint2* ref_src;  // references of the source step
+  uint2* ref_dst;        // references written by this step
+};
+
+// General pull (y or z face, or any node when `all` paths are wanted):
+// resolves the source like pull_general and decodes with the writer's
+// reference.
+__device__ __noinline__ float pull_general_ref(const __half* __restrict__ src,
+                                               const uint2* __restrict__ ref, int64_t qstride,
+                                               int nx, int ny, int nz, int pitch, int plane,
+                                               unsigned facebits, int q, int x, int y, int z,
+                                               int i, float lid, float rho0) {
+  int s0 = x - cx(q), s1 = y - cy(q), s2 = z - cz(q);
+  bool bounce = false, islid = false;
+  if (s0 < 0 || s0 >= nx) {
+    const int k = (facebits >> (s0 < 0 ? 0 : 2)) & 3;
+    if (k == BC_PERIODIC) s0 += s0 < 0 ? nx : -nx;
+    else { bounce = true; islid = k == BC_LID; }
+  }
+  if (s1 < 0 || s1 >= ny) {
+    const int k = (facebits >> (s1 < 0 ? 4 : 6)) & 3;
+    if (k == BC_PERIODIC) s1 += s1 < 0 ? ny : -ny;
+    else { bounce = true; islid = islid || k == BC_LID; }
+  }
+  if (s2 < 0 || s2 >= nz) {
+    const int k = (facebits >> (s2 < 0 ? 8 : 10)) & 3;
+    if (k == BC_PERIODIC) s2 += s2 < 0 ? nz : -nz;
+    else { bounce = true; islid = islid || k == BC_LID; }
+  }
+  if (bounce) {
+    const int qb = opp(q);
+    const float v = dec16(src[int64_t(qb) * qstride + i]) + ref_term(qb, ref_load(ref + i), rho0);
+    return islid ? v + lid : v;
+  }
+  const int j = s2 * plane + s1 * pitch + s0;
+  return dec16(src[int64_t(q) * qstride + j]) + ref_term(q, ref_load(ref + j), rho0);
+}
+
+template <bool FORCE, bool CHECK, bool CAP>
+__global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepArgs<__half, float> a,
+                                                                    const RefArgs r) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  const bool active = x < a.nx && y < a.ny;
+  if (!CHECK && !active) return;
+  const float rho0 = a.C.rho0;
+  double du2 = 0.0, uu = 0.0, dr = 0.0;
+  int bad = 0;
+  if (active) {
+    const int i = z * a.plane + y * a.pitch + x;
+    float d[Q];
+    if (y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        d[q] = dec16(a.srcq[q][i]) + ref_term(q, ref_load(r.refq[q] + i), rho0);
+      if (x == 0 || x == a.nx - 1) {
+        const int kl = a.facebits & 3, kr = (a.facebits >> 2) & 3;
+#pragma unroll
+        for (int q = 1; q < Q; ++q) {
+          const bool left = cx(q) == 1 && x == 0, right = cx(q) == -1 && x == a.nx - 1;
+          if (left || right) {
+            const int k = left ? kl : kr;
+            if (k == BC_PERIODIC) {
+              const int j = left ? i + a.nx : i - a.nx;
+              d[q] = dec16(a.srcq[q][j]) + ref_term(q, ref_load(r.refq[q] + j), rho0);
+            } else {
+              d[q] = dec16(a.src[opp(q) * a.qstride + i]) +
+                     ref_term(opp(q), ref_load(r.ref_src + i), rho0) +
+                     (k == BC_LID ? a.lidc[q] : 0.0f);
+            }
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        d[q] = pull_general_ref(a.src, r.ref_src, a.qstride, a.nx, a.ny, a.nz, a.pitch, a.plane,
+                                a.facebits, q, x, y, z, i, a.lidc[q], rho0);
+    }
+    NodeOut<float> o;
+    collide<float, FORCE>(a.C, d, o);
+    Ref4 rr;
+    r.ref_dst[i] = ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rr);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) a.dstq[q][i] = enc16(d[q] - ref_term(q, rr, rho0));
+    if (CHECK) {
+      float* up = reinterpret_cast<float*>(a.cb.uprev);
+      const int64_t nst = int64_t(a.plane) * a.nz;
+      const float px = up[i], py = up[nst + i], pz = up[2 * nst + i];
+      up[i] = o.ux;
+      up[nst + i] = o.uy;
+      up[2 * nst + i] = o.uz;
+      const double ex = double(o.ux) - double(px), ey = double(o.uy) - double(py),
+                   ez = double(o.uz) - double(pz);
+      du2 = ex * ex + ey * ey + ez * ez;
+      uu = double(o.ux) * double(o.ux) + double(o.uy) * double(o.uy) + double(o.uz) * double(o.uz);
+      dr = double(o.rho) - double(rho0);
+      const double chk = double(o.rho) + double(o.ux) + double(o.uy) + double(o.uz);
+      bad = !(chk == chk) || !(fabs(chk) < 1e30) || !(double(o.rho) > 0.5 && double(o.rho) < 2.0);
+    }
+  }
+  if (CHECK) {
+    __shared__ double smem[32];
+    block_sum_add(du2, &a.cb.acc[0], smem);
+    block_sum_add(uu, &a.cb.acc[1], smem);
+    block_sum_add(dr, &a.cb.acc[2], smem);
+    if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(a.cb.flag, 1);
+  }
+}
+
+template <bool FORCE>
+__global__ void __launch_bounds__(256) fields_ref_kernel(const __half* __restrict__ src,
+                                                         const uint2* __restrict__ ref, Geom g,
+                                                         CollideConst<float> C,
+                                                         const float* __restrict__ lidc,
+                                                         double* rho, double* u, double* gd) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= g.nx || y >= g.ny) return;
+  const int i = z * int(g.plane) + y * g.pitch + x;
+  float d[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    d[q] = pull_general_ref(src, ref, g.qstride, g.nx, g.ny, g.nz, g.pitch, int(g.plane),
+                            g.facebits, q, x, y, z, i, lidc[q], C.rho0);
+  NodeOut<float> o;
+  collide<float, FORCE>(C, d, o);
+  const int64_t N = int64_t(g.nx) * g.ny * g.nz;
+  const int64_t k = (int64_t(z) * g.ny + y) * g.nx + x;
+  if (rho) rho[k] = double(o.rho);
+  if (u) {
+    u[k] = double(o.ux);
+    u[N + k] = double(o.uy);
+    u[2 * N + k] = double(o.uz);
+  }
+  if (gd) gd[k] = double(o.gamma_dot);
+}
+
+__global__ void export_ref_kernel(const __half* __restrict__ src, const uint2* __restrict__ ref,
+                                  Geom g, float rho0, double* __restrict__ out) {
+  const int64_t N = int64_t(g.nx) * g.ny * g.nz;
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= N * Q) return;
+  const int q = int(t / N);
+  const int64_t k = t - int64_t(q) * N;
+  const int x = int(k % g.nx), y = int((k / g.nx) % g.ny), z = int(k / (int64_t(g.nx) * g.ny));
+  const int64_t i = int64_t(z) * g.plane + int64_t(y) * g.pitch + x;
+  const float dev = dec16(src[q * g.qstride + i]) + ref_term(q, ref_load(ref + i), rho0);
+  out[t] = double(dev) + wt<double>(q) * double(rho0);
+}
+
+// One thread per node: the reference is the node's own moments of the
+// imported populations.
+__global__ void import_ref_kernel(const double* __restrict__ in, Geom g, float rho0,
+                                  __half* __restrict__ dst, uint2* __restrict__ ref) {
+  const int64_t N = int64_t(g.nx) * g.ny * g.nz;
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  const int x = int(k % g.nx), y = int((k / g.nx) % g.ny), z = int(k / (int64_t(g.nx) * g.ny));
+  const int64_t i = int64_t(z) * g.plane + int64_t(y) * g.pitch + x;
+  double f[Q], rho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    f[q] = in[q * N + k];
+    rho += f[q];
+    jx += cx(q) * f[q];
+    jy += cy(q) * f[q];
+    jz += cz(q) * f[q];
+  }
+  Ref4 rr;
+  ref[i] = ref_pack(float(rho - rho0), float(jx / rho), float(jy / rho), float(jz / rho), rr);
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+    dst[q * g.qstride + i] =
+        enc16(float(f[q] - wt<double>(q) * rho0) - ref_term(q, rr, rho0));
+}
+
+// M independent nodes: store (with its own reference), load, collide, store
+// again with the new reference, load.
+template <bool FORCE>
+__global__ void collide_nodes_ref_kernel(CollideConst<float> C, const double* __restrict__ fin,
+                                         double* __restrict__ fout, double* rho, double* u,
+                                         double* gd, int64_t M) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= M) return;
+  const float rho0 = C.rho0;
+  double r0 = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const double v = fin[q * M + k];
+    r0 += v;
+    jx += cx(q) * v;
+    jy += cy(q) * v;
+    jz += cz(q) * v;
+  }
+  Ref4 rr;
+  ref_pack(float(r0 - rho0), float(jx / r0), float(jy / r0), float(jz / r0), rr);
+  float d[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const float t = ref_term(q, rr, rho0);
+    d[q] = dec16(enc16(float(fin[q * M + k] - wt<double>(q) * rho0) - t)) + t;
+  }
+  NodeOut<float> o;
+  collide<float, FORCE>(C, d, o);
+  ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rr);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const float t = ref_term(q, rr, rho0);
+    fout[q * M + k] = double(dec16(enc16(d[q] - t)) + t) + wt<double>(q) * double(rho0);
+  }
+  if (rho) rho[k] = double(o.rho);
+  if (u) {
+    u[k] = double(o.ux);
+    u[M + k] = double(o.uy);
+    u[2 * M + k] = double(o.uz);
+  }
+  if (gd) gd[k] = double(o.gamma_dot);
+}
+
+void lid_table(const Geom& g, float* out) {
+  for (int q = 0; q < Q; ++q)
+    out[q] = float(6.0 * wt<double>(q) * g.rho0 * (cx(q) * g.U[0] + cy(q) * g.U[1] + cz(q) * g.U[2]));
+}
+
+}  // namespace
+
+cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, void* ref_dst,
+                             const Geom& g, const PhysParams& P, const CheckBufs& cb, bool check,
+                             dim3 block, int npt, cudaStream_t st) {
+  StepArgs<__half, float> a;
+  RefArgs r;
+  const __half* s = static_cast<const __half*>(src);
+  __half* d = static_cast<__half*>(dst);
+  const uint2* rs = static_cast<const uint2*>(ref_src);
+  for (int q = 0; q < Q; ++q) {
+    const int64_t off = int64_t(cz(q)) * g.plane + int64_t(cy(q)) * g.pitch + cx(q);
+    a.srcq[q] = reinterpret_cast<const __half*>(reinterpret_cast<uintptr_t>(s) +
+                                                 (int64_t(q) * g.qstride - off) * 2);
+    a.dstq[q] = d + int64_t(q) * g.qstride;
+    r.refq[q] = reinterpret_cast<const uint2*>(reinterpret_cast<uintptr_t>(rs) - off * 8);
+  }
+  lid_table(g, a.lidc);
+  r.ref_src = rs;
+  r.ref_dst = static_cast<uint2*>(ref_dst);
+  a.src = s;
+  a.qstride = g.qstride;
+  a.nx = g.nx;
+  a.ny = g.ny;
+  a.nz = g.nz;
+  a.pitch = g.pitch;
+  a.plane = int(g.plane);
+  a.facebits = g.facebits;
+  a.C = make_const<float>(P);
+  a.cb = cb;
+  const bool cap = (npt & 4) != 0;
+  dim3 grid((g.nx + block.x - 1) / block.x, (g.ny + block.y - 1) / block.y, g.nz);
+#define CLBM_REF_LAUNCH(F, C_)                                                                  \
+  do {                                                                                         \
+    if (cap) step_ref_kernel<F, C_, true><<<grid, block, 0, st>>>(a, r);                       \
+    else step_ref_kernel<F, C_, false><<<grid, block, 0, st>>>(a, r);                          \
+  } while (0)
+  if (P.has_force) {
+    if (check) CLBM_REF_LAUNCH(true, true);
+    else CLBM_REF_LAUNCH(true, false);
+  } else {
+    if (check) CLBM_REF_LAUNCH(false, true);
+    else CLBM_REF_LAUNCH(false, false);
+  }
+#undef CLBM_REF_LAUNCH
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fields_f16r(const void* src, const void* ref, const Geom& g,
+                               const PhysParams& P, double* rho, double* u, double* gd,
+                               cudaStream_t st) {
+  float lid[Q];
+  lid_table(g, lid);
+  float* dlid = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&dlid), sizeof(lid), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(dlid, lid, sizeof(lid), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    dim3 block(32, 4);
+    dim3 grid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz);
+    const CollideConst<float> C = make_const<float>(P);
+    const __half* s = static_cast<const __half*>(src);
+    const uint2* r = static_cast<const uint2*>(ref);
+    if (P.has_force) fields_ref_kernel<true><<<grid, block, 0, st>>>(s, r, g, C, dlid, rho, u, gd);
+    else fields_ref_kernel<false><<<grid, block, 0, st>>>(s, r, g, C, dlid, rho, u, gd);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(dlid, st);
+  return e;
+}
+
+cudaError_t launch_export_f16r(const void* src, const void* ref, const Geom& g, double rho0,
+                               double* out, cudaStream_t st) {
+  const int64_t total = int64_t(g.nx) * g.ny * g.nz * Q;
+  const int b = 256;
+  export_ref_kernel<<<unsigned((total + b - 1) / b), b, 0, st>>>(
+      static_cast<const __half*>(src), static_cast<const uint2*>(ref), g, float(rho0), out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_import_f16r(const double* in, const Geom& g, double rho0, void* dst, void* ref,
+                               cudaStream_t st) {
+  const int64_t N = int64_t(g.nx) * g.ny * g.nz;
+  const int b = 128;
+  import_ref_kernel<<<unsigned((N + b - 1) / b), b, 0, st>>>(in, g, float(rho0),
+                                                              static_cast<__half*>(dst),
+                                                              static_cast<uint2*>(ref));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collide_nodes_f16r(const PhysParams& P, const double* fin, double* fout,
+                                      double* rho, double* u, double* gd, int64_t M,
+                                      cudaStream_t st) {
+  const int b = 128;
+  const unsigned grid = unsigned((M + b - 1) / b);
+  const CollideConst<float> C = make_const<float>(P);
+  if (P.has_force) collide_nodes_ref_kernel<true><<<grid, b, 0, st>>>(C, fin, fout, rho, u, gd, M);
+  else collide_nodes_ref_kernel<false><<<grid, b, 0, st>>>(C, fin, fout, rho, u, gd, M);
+  return cudaGetLastError();
+}
+
+}  // namespace clbm
