@@ -181,6 +181,41 @@ __device__ __noinline__ R pull_general(const S* __restrict__ src, int64_t qstrid
   return Codec<S, R>::dec(src[int64_t(q) * qstride + s2 * plane + s1 * pitch + s0], R(1));
 }
 
+// Programmatic dependent launch between consecutive steps.  A step launched
+// with the programmatic stream-serialisation attribute may be scheduled
+// while the previous step's last blocks still run: each of its threads waits
+// here until the previous grid has completed and its writes are visible,
+// before any global access, and then allows the next step to be scheduled.
+// The next grid is only scheduled once every block of this one has passed
+// this point (or exited), so its waiting blocks never take SM slots that a
+// block of this grid still needs.  Without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+// Launch a kernel whose threads start with pdl_enter(), with the programmatic
+// stream-serialisation attribute (compiled out with -DCLBM_NO_PDL).
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                              const Args&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+#ifdef CLBM_NO_PDL
+  cfg.numAttrs = 0;
+#else
+  cfg.numAttrs = 1;
+#endif
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // One time step.  Warps off the y and z faces load all 19 upwind values
 // unconditionally and then, in the one or two lanes on an x face, replace the
 // five directions that come from outside the box; warps on a y or z face go
@@ -192,6 +227,7 @@ __device__ __noinline__ R pull_general(const S* __restrict__ src, int64_t qstrid
 // spills; the autotuner decides.
 template <typename S, typename R, bool FORCE, bool CHECK, bool CAP>
 __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_kernel(const StepArgs<S, R> a) {
+  pdl_enter();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -266,6 +302,7 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_kernel(const StepArgs<S
 // touches a y or z face pulls node by node through pull_general.
 template <typename S, bool FORCE, bool CHECK, bool CAP>
 __global__ void __launch_bounds__(128, CAP ? 4 : 1) step2_kernel(const StepArgs<S, float> a) {
+  pdl_enter();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = 2 * (blockIdx.y * blockDim.y + threadIdx.y);
   const int z = blockIdx.z;
@@ -478,33 +515,35 @@ cudaError_t launch_step_t(const void* src, void* dst, const Geom& g, const PhysP
   do {                                                                                     \
     if (P.has_force) {                                                                     \
       if (check) {                                                                         \
-        if (cap) KERNEL<__VA_ARGS__, true, true, true><<<GRID, block, 0, st>>>(a);         \
-        else KERNEL<__VA_ARGS__, true, true, false><<<GRID, block, 0, st>>>(a);            \
+        if (cap) e_ = pdl_launch(KERNEL<__VA_ARGS__, true, true, true>, GRID, block, st, a);         \
+        else e_ = pdl_launch(KERNEL<__VA_ARGS__, true, true, false>, GRID, block, st, a);            \
       } else {                                                                             \
-        if (cap) KERNEL<__VA_ARGS__, true, false, true><<<GRID, block, 0, st>>>(a);        \
-        else KERNEL<__VA_ARGS__, true, false, false><<<GRID, block, 0, st>>>(a);           \
+        if (cap) e_ = pdl_launch(KERNEL<__VA_ARGS__, true, false, true>, GRID, block, st, a);        \
+        else e_ = pdl_launch(KERNEL<__VA_ARGS__, true, false, false>, GRID, block, st, a);           \
       }                                                                                    \
     } else {                                                                               \
       if (check) {                                                                         \
-        if (cap) KERNEL<__VA_ARGS__, false, true, true><<<GRID, block, 0, st>>>(a);        \
-        else KERNEL<__VA_ARGS__, false, true, false><<<GRID, block, 0, st>>>(a);           \
+        if (cap) e_ = pdl_launch(KERNEL<__VA_ARGS__, false, true, true>, GRID, block, st, a);        \
+        else e_ = pdl_launch(KERNEL<__VA_ARGS__, false, true, false>, GRID, block, st, a);           \
       } else {                                                                             \
-        if (cap) KERNEL<__VA_ARGS__, false, false, true><<<GRID, block, 0, st>>>(a);       \
-        else KERNEL<__VA_ARGS__, false, false, false><<<GRID, block, 0, st>>>(a);          \
+        if (cap) e_ = pdl_launch(KERNEL<__VA_ARGS__, false, false, true>, GRID, block, st, a);       \
+        else e_ = pdl_launch(KERNEL<__VA_ARGS__, false, false, false>, GRID, block, st, a);          \
       }                                                                                    \
     }                                                                                      \
   } while (0)
   if constexpr (std::is_same<R, float>::value) {
     if (npt == 2) {
       dim3 grid2((g.nx + block.x - 1) / block.x, (g.ny + 2 * block.y - 1) / (2 * block.y), g.nz);
+      cudaError_t e_ = cudaSuccess;
       CLBM_STEP_LAUNCH(step2_kernel, grid2, S);
-      return cudaGetLastError();
+      return e_ != cudaSuccess ? e_ : cudaGetLastError();
     }
   }
   dim3 grid((g.nx + block.x - 1) / block.x, (g.ny + block.y - 1) / block.y, g.nz);
+  cudaError_t e_ = cudaSuccess;
   CLBM_STEP_LAUNCH(step_kernel, grid, S, R);
 #undef CLBM_STEP_LAUNCH
-  return cudaGetLastError();
+  return e_ != cudaSuccess ? e_ : cudaGetLastError();
 }
 
 template <typename S, typename R>

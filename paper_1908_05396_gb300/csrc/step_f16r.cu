@@ -91,6 +91,7 @@ __device__ __noinline__ float pull_general_ref(const __half* __restrict__ src,
 template <bool FORCE, bool CHECK, bool CAP>
 __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepArgs<__half, float> a,
                                                                     const RefArgs r) {
+  pdl_enter();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -309,10 +310,11 @@ cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, vo
   a.cb = cb;
   const bool cap = (npt & 4) != 0;
   dim3 grid((g.nx + block.x - 1) / block.x, (g.ny + block.y - 1) / block.y, g.nz);
+  cudaError_t e_ = cudaSuccess;
 #define CLBM_REF_LAUNCH(F, C_)                                                                  \
   do {                                                                                         \
-    if (cap) step_ref_kernel<F, C_, true><<<grid, block, 0, st>>>(a, r);                       \
-    else step_ref_kernel<F, C_, false><<<grid, block, 0, st>>>(a, r);                          \
+    if (cap) e_ = pdl_launch(step_ref_kernel<F, C_, true>, grid, block, st, a, r);            \
+    else e_ = pdl_launch(step_ref_kernel<F, C_, false>, grid, block, st, a, r);               \
   } while (0)
   if (P.has_force) {
     if (check) CLBM_REF_LAUNCH(true, true);
@@ -322,7 +324,7 @@ cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, vo
     else CLBM_REF_LAUNCH(false, false);
   }
 #undef CLBM_REF_LAUNCH
-  return cudaGetLastError();
+  return e_ != cudaSuccess ? e_ : cudaGetLastError();
 }
 
 cudaError_t launch_fields_f16r(const void* src, const void* ref, const Geom& g,
