@@ -109,19 +109,25 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def _traffic_note(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the
-    current kernel sources (else null)."""
+def kernel_source_hash() -> str:
+    """Hash of the sources that define the FP32 step kernels (the headers and
+    the FP32 translation unit), so that host-side changes keep a capture valid."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
-    if not os.path.exists(path):
-        return None
     csrc = os.path.join(ROOT, "paper_1908_05396_gb300", "csrc")
     h = hashlib.sha256()
     for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
+        if fn.endswith((".cuh", ".h")) or fn == "step_f32.cu":
             h.update(open(os.path.join(csrc, fn), "rb").read())
-    digest = h.hexdigest()[:16]
+    return h.hexdigest()[:16]
+
+
+def _traffic_note(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the
+    current kernel sources (else null)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    digest = kernel_source_hash()
     for line in open(path):
         parts = line.split()
         if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
