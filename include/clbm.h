@@ -146,7 +146,9 @@ int clbm_destroy(clbm_handle h);
 
 /* Pick the launch shape of h's step kernel by timing: thread-block shapes
  * from 32x1 to 256x1 and, for the FP32-math forms, one or two nodes per
- * thread (two nodes are collided together with packed FP32 instructions).
+ * thread (two nodes are collided together with packed FP32 instructions),
+ * with and without a 64-register cap; for FP32 and F16S storage also the
+ * TMA-staged kernel in each of its shapes (see clbm_set_launch).
  * Each candidate runs `steps` steps (<= 0 -> 10) after two warm-up steps,
  * timed with CUDA events on the handle's stream; the state is saved first
  * and restored afterwards, and the step counter does not move.  The choice
@@ -159,7 +161,18 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
 
 /* Set the launch shape of h's step kernel directly: block_x * block_y
  * threads (a multiple of 32, at most 256; at most 128 when npt = 2) and
- * npt = 1 or 2 nodes per thread (2 only for the FP32 and F16S forms). */
+ * npt = 1 or 2 nodes per thread (2 only for the FP32 and F16S forms), plus 4
+ * for the register-capped variant.  FP32 and F16S storage also take
+ * npt = 16 + 32 v, the kernel whose upwind populations are staged in shared
+ * memory by TMA loads, in shape v (block, nodes per thread): v = 0: 64x4, 1;
+ * v = 1: 128x2, 1; v = 2: 32x8, 1; v = 3: 64x4, 1 (three ring stages);
+ * v = 4: 32x4, 1; v = 5: 64x2, 1; v = 6: 64x2, 2; v = 7: 32x4, 2; v = 8:
+ * 64x2, 2 (four CTAs per SM); v = 9: 128x1, 2.  With two nodes a thread
+ * collides rows 2y and 2y+1 as a packed FP32 pair.  block_x x block_y must
+ * be that shape's.  Check steps run
+ * the plain kernel with the same block.  If a pipeline wait of that kernel
+ * gives up (about one second; never expected), the next check makes
+ * clbm_step / clbm_residual return CLBM_ERR_CUDA. */
 int clbm_set_launch(clbm_handle h, int block_x, int block_y, int npt);
 
 /* ---- Batched stepping of many lattices --------------------------------

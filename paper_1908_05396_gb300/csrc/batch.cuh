@@ -63,10 +63,8 @@ __device__ __forceinline__ void batch_node(const LatDesc<R>& L, const S* __restr
       }
     }
   } else {
-#pragma unroll
-    for (int q = 0; q < Q; ++q)
-      d[q] = pull_general<S, R>(src, L.qstride, L.nx, L.ny, L.nz, pitch, plane, L.facebits, q,
-                                x, y, z, i, L.lidc[q]);
+    pull_face<S, R>(src, L.qstride, L.nx, L.ny, L.nz, pitch, plane, L.facebits, x, y, z, i,
+                    L.lidc, d);
   }
   collide<R, FORCE>(L.C, d, o);
 #pragma unroll

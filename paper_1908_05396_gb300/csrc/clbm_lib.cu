@@ -205,6 +205,7 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
   }
   e = cudaMalloc(&h->uprev, 3 * size_t(g.plane) * g.nz * h->rsize);
   if (e != cudaSuccess) return cleanup(CLBM_ERR_OOM, "velocity buffer allocation failed");
+  // acc: 3 FP64 sums, then the divergence flag and the TMA error word
   e = cudaMalloc(&h->acc, 4 * sizeof(double));
   if (e != cudaSuccess) return cleanup(CLBM_ERR_OOM, "reduction buffer allocation failed");
   h->flag = reinterpret_cast<int*>(h->acc + 3);
@@ -246,10 +247,13 @@ int clbm_step(clbm_handle h, int64_t nsteps) {
     }
   }
   if (!h->diverged && h->checks > 0 && cudaEventQuery(h->check_done) == cudaSuccess) {
-    int f = 0;
-    std::memcpy(&f, &h->host[3], sizeof(int));
-    h->diverged = f != 0;
+    int f[2] = {0, 0};
+    std::memcpy(f, &h->host[3], sizeof(f));
+    h->diverged = f[0] != 0;
+    h->pipeline_err = h->pipeline_err || f[1] != 0;
   }
+  if (h->pipeline_err)
+    return fail(h, CLBM_ERR_CUDA, "a TMA pipeline wait in the step kernel gave up");
   if (h->diverged)
     return fail(h, CLBM_ERR_DIVERGED, "divergence: non-finite value or density out of [0.5, 2]");
   return CLBM_OK;
@@ -312,9 +316,12 @@ int clbm_residual(clbm_handle h, double* out) {
   } else {
     *out = std::sqrt(h->host[0]) / (double(h->dom.check_interval) * std::sqrt(h->host[1]));
   }
-  int f = 0;
-  std::memcpy(&f, &h->host[3], sizeof(int));
-  h->diverged = h->diverged || f != 0;
+  int f[2] = {0, 0};
+  std::memcpy(f, &h->host[3], sizeof(f));
+  h->diverged = h->diverged || f[0] != 0;
+  h->pipeline_err = h->pipeline_err || f[1] != 0;
+  if (h->pipeline_err)
+    return fail(h, CLBM_ERR_CUDA, "a TMA pipeline wait in the step kernel gave up");
   if (h->diverged)
     return fail(h, CLBM_ERR_DIVERGED, "divergence: non-finite value or density out of [0.5, 2]");
   return CLBM_OK;
@@ -426,6 +433,9 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
         if (sh[0] > 32 && sh[0] > h->g.pitch) continue;
         cands.push_back({sh[0], sh[1], np + 4 * capped});
       }
+  // FP32 and FP16 storage: the TMA-staged kernel in each of its shapes
+  if (h->dtype == CLBM_F32 || h->dtype == CLBM_F16S)
+    for (int v = 0; v < TMA_NVAR; ++v) cands.push_back({tma_bx(v), tma_by(v), TMA_NPT + 32 * v});
   // Save the state: tuning runs real steps.
   const size_t pop_bytes = size_t(NQ) * size_t(h->g.qstride) * h->elem;
   const size_t ref_bytes = h->ref[0] ? (size_t(h->g.plane) * h->g.nz + 64) * 8 : 0;
@@ -499,6 +509,18 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
 
 int clbm_set_launch(clbm_handle h, int block_x, int block_y, int npt) {
   if (bad(h)) return fail(h, CLBM_ERR_ARG, "invalid handle");
+  if (npt & TMA_NPT) {
+    const int v = npt >> 5;
+    if ((npt & 31) != TMA_NPT || v >= TMA_NVAR)
+      return fail(h, CLBM_ERR_ARG, "npt: TMA_NPT + 32 v with v < TMA_NVAR for the TMA kernel");
+    if (h->dtype != CLBM_F32 && h->dtype != CLBM_F16S)
+      return fail(h, CLBM_ERR_UNSUPPORTED, "the TMA-staged kernel takes FP32 or F16S storage");
+    if (block_x != tma_bx(v) || block_y != tma_by(v))
+      return fail(h, CLBM_ERR_ARG, "block does not match the TMA shape");
+    h->block = dim3(block_x, block_y, 1);
+    h->npt = npt;
+    return CLBM_OK;
+  }
   const int np = npt & 3;
   if ((np != 1 && np != 2) || (npt & ~7))
     return fail(h, CLBM_ERR_ARG, "npt must be 1 or 2, plus 4 for the register-capped kernel");

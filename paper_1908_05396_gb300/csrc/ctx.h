@@ -20,7 +20,7 @@ struct clbm_ctx {
   void* ref[2] = {nullptr, nullptr};  // F16R: per-node reference moments, with buf
   int cur = 0;           // buffer holding the current state
   void* uprev = nullptr;
-  double* acc = nullptr; // device: 3 doubles, then the int flag
+  double* acc = nullptr; // device: 3 doubles, then the int flag and the TMA error word
   int* flag = nullptr;
   double* host = nullptr; // pinned: acc[3], flag as double
   cudaEvent_t check_done = nullptr;
@@ -29,8 +29,10 @@ struct clbm_ctx {
   int64_t steps = 0;
   int64_t checks = 0;    // check steps queued so far
   bool diverged = false; // sticky once a completed check saw divergence
+  bool pipeline_err = false; // sticky once a check saw a TMA wait give up
   dim3 block{32, 4, 1};
-  int npt = 1;           // nodes per thread (1 or 2), + 4 for the register-capped kernel
+  int npt = 1;           // nodes per thread (1 or 2), + 4 for the register-capped kernel,
+                         // or TMA_NPT + 32 v for the TMA-staged kernel of shape v
   struct clbm_batch_ctx* batch = nullptr;  // batch stepping this lattice, if any
   std::string err;
 };

@@ -149,36 +149,71 @@ struct StepArgs {
   CheckBufs cb;
 };
 
-// Pull of direction q into node (x, y, z) for nodes on a y or z face, where
-// any of the three source coordinates may leave the box.  Not inlined: it
-// runs only in warps on those faces, and one shared copy keeps the step
-// kernel small enough for the instruction cache.
+// Pull of all 19 directions into node (x, y, z) with index i, for a node on
+// any face.  A direction whose upwind node lies inside the lattice is loaded
+// as in the interior (its address is formed only then); the others follow the
+// face rules -- the periodic wrap along a periodic axis, or else (any crossed
+// wall or lid face) halfway bounce-back from the node's own opposite
+// population, plus the lid term when a crossed face is the lid.  With the directions unrolled, a warp on a face issues one load per
+// direction instead of a call with table lookups.
 template <typename S, typename R>
-__device__ __noinline__ R pull_general(const S* __restrict__ src, int64_t qstride, int nx,
-                                       int ny, int nz, int pitch, int plane, unsigned facebits,
-                                       int q, int x, int y, int z, int i, R lid) {
-  int s0 = x - c_ex[q], s1 = y - c_ey[q], s2 = z - c_ez[q];
-  bool bounce = false, islid = false;
-  if (s0 < 0 || s0 >= nx) {
-    const int k = (facebits >> (s0 < 0 ? 0 : 2)) & 3;
-    if (k == BC_PERIODIC) s0 += s0 < 0 ? nx : -nx;
-    else { bounce = true; islid = k == BC_LID; }
+__device__ __forceinline__ void pull_face(const S* __restrict__ src, int64_t qstride, int nx,
+                                          int ny, int nz, int pitch, int plane, unsigned fb,
+                                          int x, int y, int z, int i, const R* lidc, R (&d)[Q]) {
+  const bool fx0 = x == 0, fx1 = x == nx - 1, fy0 = y == 0, fy1 = y == ny - 1;
+  const bool fz0 = z == 0, fz1 = z == nz - 1;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const S* sq = src + int64_t(q) * qstride;
+    const bool ox = (cx(q) == 1 && fx0) || (cx(q) == -1 && fx1);
+    const bool oy = (cy(q) == 1 && fy0) || (cy(q) == -1 && fy1);
+    const bool oz = (cz(q) == 1 && fz0) || (cz(q) == -1 && fz1);
+    const int up = i - (cz(q) * plane + cy(q) * pitch + cx(q));
+    if (!(ox || oy || oz)) {
+      d[q] = Codec<S, R>::dec(sq[up], R(1));
+      continue;
+    }
+    // kind of each crossed face (faces -x, +x, -y, +y, -z, +z, two bits each)
+    const int kx = ox ? int((fb >> (cx(q) == 1 ? 0 : 2)) & 3u) : int(BC_PERIODIC);
+    const int ky = oy ? int((fb >> (cy(q) == 1 ? 4 : 6)) & 3u) : int(BC_PERIODIC);
+    const int kz = oz ? int((fb >> (cz(q) == 1 ? 8 : 10)) & 3u) : int(BC_PERIODIC);
+    if (kx != BC_PERIODIC || ky != BC_PERIODIC || kz != BC_PERIODIC) {
+      const bool lid = kx == BC_LID || ky == BC_LID || kz == BC_LID;
+      const R v = Codec<S, R>::dec(src[int64_t(opp(q)) * qstride + i], R(1));
+      d[q] = lid ? v + lidc[q] : v;
+    } else {
+      int j = up;
+      if (ox) j += cx(q) == 1 ? nx : -nx;
+      if (oy) j += cy(q) == 1 ? ny * pitch : -ny * pitch;
+      if (oz) j += cz(q) == 1 ? nz * plane : -nz * plane;
+      d[q] = Codec<S, R>::dec(sq[j], R(1));
+    }
   }
-  if (s1 < 0 || s1 >= ny) {
-    const int k = (facebits >> (s1 < 0 ? 4 : 6)) & 3;
-    if (k == BC_PERIODIC) s1 += s1 < 0 ? ny : -ny;
-    else { bounce = true; islid = islid || k == BC_LID; }
+}
+
+// For a node off the y and z faces whose d[] holds the plain upwind values:
+// replace the directions that cross an x face (bounce-back with the lid term,
+// or the periodic wrap).  Only lanes at x = 0 or x = nx - 1 do any work.
+template <typename S, typename R>
+__device__ __forceinline__ void xface_fix(const StepArgs<S, R>& a, int x, int i, R (&d)[Q]) {
+  if (x == 0 || x == a.nx - 1) {
+    const int kl = a.facebits & 3, kr = (a.facebits >> 2) & 3;
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+      if (cx(q) == 1 && x == 0) {
+        d[q] = kl == BC_PERIODIC
+                   ? Codec<S, R>::dec(a.srcq[q][i + a.nx], R(1))
+                   : Codec<S, R>::dec(a.src[opp(q) * a.qstride + i], R(1)) +
+                         (kl == BC_LID ? a.lidc[q] : R(0));
+      }
+      if (cx(q) == -1 && x == a.nx - 1) {
+        d[q] = kr == BC_PERIODIC
+                   ? Codec<S, R>::dec(a.srcq[q][i - a.nx], R(1))
+                   : Codec<S, R>::dec(a.src[opp(q) * a.qstride + i], R(1)) +
+                         (kr == BC_LID ? a.lidc[q] : R(0));
+      }
+    }
   }
-  if (s2 < 0 || s2 >= nz) {
-    const int k = (facebits >> (s2 < 0 ? 8 : 10)) & 3;
-    if (k == BC_PERIODIC) s2 += s2 < 0 ? nz : -nz;
-    else { bounce = true; islid = islid || k == BC_LID; }
-  }
-  if (bounce) {
-    R v = Codec<S, R>::dec(src[int64_t(c_opp[q]) * qstride + i], R(1));
-    return islid ? v + lid : v;
-  }
-  return Codec<S, R>::dec(src[int64_t(q) * qstride + s2 * plane + s1 * pitch + s0], R(1));
 }
 
 // Programmatic dependent launch between consecutive steps.  A step launched
@@ -219,7 +254,7 @@ inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, c
 // One time step.  Warps off the y and z faces load all 19 upwind values
 // unconditionally and then, in the one or two lanes on an x face, replace the
 // five directions that come from outside the box; warps on a y or z face go
-// through pull_general.  CHECK = true also writes u into uprev (after reading
+// through pull_face.  CHECK = true also writes u into uprev (after reading
 // the previous check's value there) and reduces sum|u - uprev|^2, sum|u|^2,
 // sum(rho - rho0) and a divergence flag in FP64.
 // CAP = true caps registers so that four 256-thread (or eight 128-thread)
@@ -241,29 +276,10 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_kernel(const StepArgs<S
     if (y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1) {
 #pragma unroll
       for (int q = 0; q < Q; ++q) d[q] = Codec<S, R>::dec(a.srcq[q][i], R(1));
-      if (x == 0 || x == a.nx - 1) {
-        const int kl = a.facebits & 3, kr = (a.facebits >> 2) & 3;
-#pragma unroll
-        for (int q = 1; q < Q; ++q) {
-          if (cx(q) == 1 && x == 0) {
-            d[q] = kl == BC_PERIODIC
-                       ? Codec<S, R>::dec(a.srcq[q][i + a.nx], R(1))
-                       : Codec<S, R>::dec(a.src[opp(q) * a.qstride + i], R(1)) +
-                             (kl == BC_LID ? a.lidc[q] : R(0));
-          }
-          if (cx(q) == -1 && x == a.nx - 1) {
-            d[q] = kr == BC_PERIODIC
-                       ? Codec<S, R>::dec(a.srcq[q][i - a.nx], R(1))
-                       : Codec<S, R>::dec(a.src[opp(q) * a.qstride + i], R(1)) +
-                             (kr == BC_LID ? a.lidc[q] : R(0));
-          }
-        }
-      }
+      xface_fix(a, x, i, d);
     } else {
-#pragma unroll
-      for (int q = 0; q < Q; ++q)
-        d[q] = pull_general<S, R>(a.src, a.qstride, a.nx, a.ny, a.nz, a.pitch, a.plane,
-                                  a.facebits, q, x, y, z, i, a.lidc[q]);
+      pull_face<S, R>(a.src, a.qstride, a.nx, a.ny, a.nz, a.pitch, a.plane, a.facebits, x, y, z,
+                      i, a.lidc, d);
     }
     NodeOut<R> o;
     collide<R, FORCE>(a.C, d, o);
@@ -299,7 +315,7 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_kernel(const StepArgs<S
 // pair with packed FP32 arithmetic (R = V2).  Loads and stores stay 32-bit
 // per row, so every warp access still covers 32 consecutive x.  Both nodes
 // share x, so the x-face replacement is the same for the pair; a pair that
-// touches a y or z face pulls node by node through pull_general.
+// touches a y or z face pulls node by node through pull_face.
 template <typename S, bool FORCE, bool CHECK, bool CAP>
 __global__ void __launch_bounds__(128, CAP ? 4 : 1) step2_kernel(const StepArgs<S, float> a) {
   pdl_enter();
@@ -344,12 +360,13 @@ __global__ void __launch_bounds__(128, CAP ? 4 : 1) step2_kernel(const StepArgs<
       }
     } else {
       const int yB = activeB ? y + 1 : y;
+      float dA[Q], dB[Q];
+      pull_face<S, float>(a.src, a.qstride, a.nx, a.ny, a.nz, a.pitch, a.plane, a.facebits, x, y,
+                          z, iA, a.lidc, dA);
+      pull_face<S, float>(a.src, a.qstride, a.nx, a.ny, a.nz, a.pitch, a.plane, a.facebits, x, yB,
+                          z, iB, a.lidc, dB);
 #pragma unroll
-      for (int q = 0; q < Q; ++q)
-        d[q] = V2(pull_general<S, float>(a.src, a.qstride, a.nx, a.ny, a.nz, a.pitch, a.plane,
-                                         a.facebits, q, x, y, z, iA, a.lidc[q]),
-                  pull_general<S, float>(a.src, a.qstride, a.nx, a.ny, a.nz, a.pitch, a.plane,
-                                         a.facebits, q, x, yB, z, iB, a.lidc[q]));
+      for (int q = 0; q < Q; ++q) d[q] = V2(dA[q], dB[q]);
     }
     NodeOut<V2> o;
     collide<V2, FORCE>(a.C, d, o);
@@ -480,6 +497,12 @@ __global__ void import_kernel(const double* __restrict__ in, Geom g, double rho0
   dst[q * g.qstride + i] = Codec<S, double>::enc(in[t] - w * rho0, inv_scale);
 }
 
+}  // namespace clbm
+
+#include "tma_step.cuh"
+
+namespace clbm {
+
 // ---- host-side launchers, instantiated once per storage type --------------
 template <typename S, typename R>
 cudaError_t launch_step_t(const void* src, void* dst, const Geom& g, const PhysParams& P,
@@ -508,7 +531,13 @@ cudaError_t launch_step_t(const void* src, void* dst, const Geom& g, const PhysP
   a.facebits = g.facebits;
   a.C = make_const<R>(P);
   a.cb = cb;
-  // npt: 1 or 2 nodes per thread; +4 selects the register-capped variant.
+  // npt: 1 or 2 nodes per thread; +4 selects the register-capped variant;
+  // TMA_NPT + 32 v the TMA-staged kernel of shape v (check steps take the
+  // plain kernel with the same block).
+  if constexpr (std::is_same<R, float>::value && !std::is_same<S, double>::value) {
+    if ((npt & TMA_NPT) && !check)
+      return launch_step_tma<S>(a, src, g, P.has_force != 0, npt >> 5, cb.flag + 1, st);
+  }
   const bool cap = (npt & 4) != 0;
   npt &= 3;
 #define CLBM_STEP_LAUNCH(KERNEL, GRID, ...)                                                 \

@@ -40,8 +40,21 @@ struct PhysParams {
 struct CheckBufs {
   void* uprev;      // 3 x (plane * nz) velocities of the previous check, math type
   double* acc;      // [0] sum|u-uprev|^2, [1] sum|u|^2, [2] sum(rho - rho0)
-  int* flag;        // divergence flag
+  int* flag;        // [0] divergence flag, [1] set when a TMA pipeline wait gave up
 };
+
+// TMA-staged FP32 / FP16 step (tma_step.cuh): npt = TMA_NPT + 32 v selects
+// shape v, whose block must be tma_bx(v) x tma_by(v).
+constexpr int TMA_NPT = 16;
+constexpr int TMA_NVAR = 10;
+// block of shape v: tiles 64x4, 128x2, 32x8, 64x4, 32x4, 64x2 with one node
+// per thread (v < 6), then 64x4, 32x8, 64x4, 128x2 with two (rows 2ty, 2ty+1)
+__host__ __device__ constexpr int tma_bx(int v) {
+  return (v == 1 || v == 9) ? 128 : (v == 2 || v == 4 || v == 7) ? 32 : 64;
+}
+__host__ __device__ constexpr int tma_by(int v) {
+  return v == 9 ? 1 : (v == 1 || v == 5 || v == 6 || v == 8) ? 2 : v == 2 ? 8 : 4;
+}
 
 // Launchers, one instantiation per storage type (one translation unit each).
 #define CLBM_DECLARE_LAUNCHERS(SUFFIX)                                                        \
