@@ -140,6 +140,39 @@ __device__ __forceinline__ double omega_nu(const CollideConst<double>& C, double
   return w;
 }
 
+// Coefficient of g^_j (j >= 4) in f~_q as the grouped back-transform in
+// collide() forms it; grouping_is_K() checks it against every entry of K.
+constexpr int grouped_coef(int q, int j) {
+  const int x = cx(q), y = cy(q), z = cz(q);
+  const int axes = (x != 0) + (y != 0) + (z != 0);
+  if (axes == 0) return j == 9 ? -30 : j == 16 ? 12 : 0;
+  if (axes == 1) {  // Ca = -11 g9 - 4 g16, then the axis's own terms
+    int c = j == 9 ? -11 : j == 16 ? -4 : 0;
+    if (x) c += (j == 7 || j == 8) ? 1 : j == 17 ? -4 : j == 10 ? -4 * x : 0;
+    if (y) c += j == 7 ? -1 : j == 8 ? 1 : j == 17 ? 2 : j == 18 ? -2 : j == 11 ? -4 * y : 0;
+    if (z) c += j == 8 ? -2 : (j == 17 || j == 18) ? 2 : j == 12 ? -4 * z : 0;
+    return c;
+  }
+  int c = j == 9 ? 8 : j == 16 ? 1 : 0;  // C9 = 8 g9 + g16
+  if (z == 0)  // xy: 2 g8 + g17 + g18 + xy g4; odd x (g10 + g13) + y (g11 - g14)
+    c += j == 8 ? 2 : (j == 17 || j == 18) ? 1 : j == 4 ? x * y : (j == 10 || j == 13) ? x
+         : j == 11 ? y : j == 14 ? -y : 0;
+  else if (y == 0)  // xz: g7 - g8 + g17 - g18 + xz g5; odd x (g10 - g13) + z (g12 + g15)
+    c += j == 7 ? 1 : j == 8 ? -1 : j == 17 ? 1 : j == 18 ? -1 : j == 5 ? x * z : j == 10 ? x
+         : j == 13 ? -x : (j == 12 || j == 15) ? z : 0;
+  else  // yz: -g7 - g8 - 2 g17 + yz g6; odd y (g11 + g14) + z (g12 - g15)
+    c += (j == 7 || j == 8) ? -1 : j == 17 ? -2 : j == 6 ? y * z : (j == 11 || j == 14) ? y
+         : j == 12 ? z : j == 15 ? -z : 0;
+  return c;
+}
+constexpr bool grouping_is_K() {
+  for (int q = 0; q < Q; ++q)
+    for (int j = 4; j < Q; ++j)
+      if (grouped_coef(q, j) != kb(j, cx(q), cy(q), cz(q))) return false;
+  return true;
+}
+static_assert(grouping_is_K(), "the grouped back-transform must reproduce K");
+
 // Collide one node.  d[19] holds the pre-collision deviations on entry and
 // the post-collision deviations f~ - w rho0 on return.
 template <typename R, bool FORCE>
@@ -251,24 +284,28 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
   const R g8 = R(-1.0 / 36.0) * w * (R(2) * m8 - m7);
   const R g9 = R(-1.0 / 126.0) * m9;
 
-  const R g10 = R(0.125) * (-(Dxyy + Dxzz) + R(2) * (uy * Dxy + uz * Dxz) + ux * (kyy + kzz) -
-                            R(2) * rho * ux * (uy2 + uz2)) +
-                (uy * g4 + uz * g5) + R(0.75) * ux * (-(g7 + g8) + R(14) * g9);
-  const R g11 = R(0.125) * (-(Dyzz + Dxxy) + R(2) * (ux * Dxy + uz * Dyz) + uy * (kxx + kzz) -
-                            R(2) * rho * uy * (ux2 + uz2)) +
-                (ux * g4 + uz * g6) + R(0.75) * uy * (g7 - g8 + R(14) * g9);
-  const R g12 = R(0.125) * (-(Dxxz + Dyyz) + R(2) * (ux * Dxz + uy * Dyz) + uz * (kxx + kyy) -
-                            R(2) * rho * uz * (ux2 + uy2)) +
-                (ux * g5 + uy * g6) + R(1.5) * uz * (g8 + R(7) * g9);
-  const R g13 = R(0.125) * (-(Dxyy - Dxzz) + R(2) * (uy * Dxy - uz * Dxz) + ux * (Dyy - Dzz) -
-                            R(2) * rho * ux * (uy2 - uz2)) +
-                (uy * g4 - uz * g5) + R(0.75) * ux * (-g7 + R(3) * g8);
-  const R g14 = R(0.125) * (-(Dyzz - Dxxy) + R(2) * (uz * Dyz - ux * Dxy) + uy * (Dzz - Dxx) -
-                            R(2) * rho * uy * (uz2 - ux2)) +
-                (-ux * g4 + uz * g6) + R(0.75) * uy * (-g7 - R(3) * g8);
-  const R g15 = R(0.125) * (-(Dxxz - Dyyz) + R(2) * (ux * Dxz - uy * Dyz) + uz * (Dxx - Dyy) -
-                            R(2) * rho * uz * (ux2 - uy2)) +
-                (ux * g5 - uy * g6) + R(1.5) * uz * g7;
+  // g^_10..15 in +/- pairs: with the row sums
+  //   Xy = ux k'yy - k'xyy + 2 uy k'xy - 2 rho ux uy^2 (and Xz, Yx, Yz, Zx, Zy
+  //   alike), the bracket of g^_10 is Xy + Xz and that of g^_13 is Xy - Xz
+  //   (k'yy - k'zz = Dyy - Dzz), and so on for 11/14 and 12/15.
+  const R tux = R(2) * ux, tuy = R(2) * uy, tuz = R(2) * uz;
+  const R rho2 = R(2) * rho;
+  const R rx2 = rho2 * ux, ry2 = rho2 * uy, rz2 = rho2 * uz;
+  const R Xy = ux * kyy - Dxyy + tuy * Dxy - rx2 * uy2;
+  const R Xz = ux * kzz - Dxzz + tuz * Dxz - rx2 * uz2;
+  const R Yx = uy * kxx - Dxxy + tux * Dxy - ry2 * ux2;
+  const R Yz = uy * kzz - Dyzz + tuz * Dyz - ry2 * uz2;
+  const R Zx = uz * kxx - Dxxz + tux * Dxz - rz2 * ux2;
+  const R Zy = uz * kyy - Dyyz + tuy * Dyz - rz2 * uy2;
+  const R a4y = uy * g4, a5z = uz * g5, a4x = ux * g4, a6z = uz * g6, a5x = ux * g5, a6y = uy * g6;
+  const R hx = R(0.75) * ux, hy = R(0.75) * uy, hz = R(1.5) * uz;
+  const R w9 = R(14) * g9;
+  const R g10 = R(0.125) * (Xy + Xz) + (a4y + a5z) + hx * (w9 - (g7 + g8));
+  const R g13 = R(0.125) * (Xy - Xz) + (a4y - a5z) + hx * (R(3) * g8 - g7);
+  const R g11 = R(0.125) * (Yx + Yz) + (a4x + a6z) + hy * (w9 + (g7 - g8));
+  const R g14 = R(0.125) * (Yz - Yx) + (a6z - a4x) - hy * (g7 + R(3) * g8);
+  const R g12 = R(0.125) * (Zx + Zy) + (a5x + a6y) + hz * (g8 + R(7) * g9);
+  const R g15 = R(0.125) * (Zx - Zy) + (a5x - a6y) + hz * g7;
 
   // Post-collision diagonal central moments k~ii = rho/3 + a_i (the <K g^|e_i^2>
   // rows of Eq. momentscascadedcollisionterm added to k'_ii - rho u_i^2), and
@@ -312,27 +349,70 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
                 uy * g11 - uz * g12 + R(2) * ux * g13 - uy * g14 - uz * g15;
 
   // ---- back-transform f~ = f + K g^ (+ second half of the source) --------
-  // Even basis vectors take the same value at e and -e, odd ones flip sign,
-  // so each +/- pair shares its even part E and odd part O.
-  const R g[Q] = {R(0), R(0), R(0), R(0), g4,  g5,  g6,  g7,  g8, g9,
-                  g10,  g11,  g12,  g13,  g14, g15, g16, g17, g18};
-  d[0] += R(kb(9, 0, 0, 0)) * g9 + R(kb(16, 0, 0, 0)) * g16;
-#pragma unroll
-  for (int p = 0; p < NPAIR; ++p) {
-    const int q = pair_pos(p);
-    const int x = cx(q), y = cy(q), z = cz(q);
-    R E = R(0), O = R(0);
-#pragma unroll
-    for (int j = 4; j < Q; ++j) {
-      const int k = kb(j, x, y, z);
-      if (k == 0) continue;
-      if (kb_odd(j))
-        O += R(k) * g[j];
-      else
-        E += R(k) * g[j];
-    }
-    d[q] += E + O;
-    d[opp(q)] += E - O;
+  // Columns of K grouped by velocity class (Sec. 2, the basis vectors): the
+  // rest node; the three axis pairs, which share -11 g9 - 4 g16; and the
+  // three coordinate planes of diagonal velocities, which share 8 g9 + g16.
+  // In a plane the four velocities differ only in the sign of the plane's
+  // product moment g4/g5/g6 (even part) and of two odd sums, e.g. in the xy
+  // plane Px = g10 + g13 (odd in x) and Py = g11 - g14 (odd in y).
+  static_assert(cx(7) == 1 && cy(7) == 1 && cx(8) == -1 && cy(8) == 1 && cx(9) == 1 &&
+                    cy(9) == -1 && cx(10) == -1 && cy(10) == -1,
+                "xy-plane velocity order");
+  static_assert(cx(11) == 1 && cz(11) == 1 && cx(12) == -1 && cz(12) == 1 && cx(13) == 1 &&
+                    cz(13) == -1 && cx(14) == -1 && cz(14) == -1,
+                "xz-plane velocity order");
+  static_assert(cy(15) == 1 && cz(15) == 1 && cy(16) == -1 && cz(16) == 1 && cy(17) == 1 &&
+                    cz(17) == -1 && cy(18) == -1 && cz(18) == -1,
+                "yz-plane velocity order");
+  static_assert(cx(1) == 1 && cx(2) == -1 && cy(3) == 1 && cy(4) == -1 && cz(5) == 1 &&
+                    cz(6) == -1,
+                "axis velocity order");
+  static_assert(kb(9, 0, 0, 0) == -30 && kb(16, 0, 0, 0) == 12 && kb(9, 1, 0, 0) == -11 &&
+                    kb(16, 1, 0, 0) == -4 && kb(9, 1, 1, 0) == 8 && kb(16, 1, 1, 0) == 1,
+                "K entries of the grouping");
+  d[0] += R(-30) * g9 + R(12) * g16;
+  const R Ca = R(-11) * g9 - R(4) * g16;
+  {
+    const R Ex = Ca + (g7 + g8) - R(4) * g17;
+    d[1] = (d[1] + Ex) - R(4) * g10;
+    d[2] = (d[2] + Ex) + R(4) * g10;
+    const R Ey = Ca + (g8 - g7) + R(2) * (g17 - g18);
+    d[3] = (d[3] + Ey) - R(4) * g11;
+    d[4] = (d[4] + Ey) + R(4) * g11;
+    const R Ez = Ca - R(2) * g8 + R(2) * (g17 + g18);
+    d[5] = (d[5] + Ez) - R(4) * g12;
+    d[6] = (d[6] + Ez) + R(4) * g12;
+  }
+  const R C9 = R(8) * g9 + g16;
+  {
+    const R E = C9 + R(2) * g8 + (g17 + g18);
+    const R Ep = E + g4, Em = E - g4;
+    const R Px = g10 + g13, Py = g11 - g14;
+    const R S = Px + Py, D = Py - Px;
+    d[7] += Ep + S;
+    d[10] += Ep - S;
+    d[8] += Em + D;
+    d[9] += Em - D;
+  }
+  {
+    const R E = C9 + (g7 - g8) + (g17 - g18);
+    const R Ep = E + g5, Em = E - g5;
+    const R Qx = g10 - g13, Qz = g12 + g15;
+    const R S = Qx + Qz, D = Qz - Qx;
+    d[11] += Ep + S;
+    d[14] += Ep - S;
+    d[12] += Em + D;
+    d[13] += Em - D;
+  }
+  {
+    const R E = C9 - (g7 + g8) - R(2) * g17;
+    const R Ep = E + g6, Em = E - g6;
+    const R Ry = g11 + g14, Rz = g12 - g15;
+    const R S = Ry + Rz, D = Rz - Ry;
+    d[15] += Ep + S;
+    d[18] += Ep - S;
+    d[16] += Em + D;
+    d[17] += Em - D;
   }
   if (FORCE) {
 #pragma unroll
