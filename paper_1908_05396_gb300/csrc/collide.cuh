@@ -180,22 +180,52 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
                                         R (&d)[Q], NodeOut<R>& out) {
   using T = typename ScalarOf<R>::type;
   // ---- mass and momentum (Eqs. hydrodynamicfields1/2) -------------------
-  R s[NPAIR], t[NPAIR];
-#pragma unroll
-  for (int p = 0; p < NPAIR; ++p) {
-    s[p] = d[pair_pos(p)] + d[opp(pair_pos(p))];
-    t[p] = d[pair_pos(p)] - d[opp(pair_pos(p))];
-  }
-  R drho = d[0];
-  R jx = R(0), jy = R(0), jz = R(0);
-#pragma unroll
-  for (int p = 0; p < NPAIR; ++p) {
-    const int q = pair_pos(p);
-    drho += s[p];
-    if (cx(q)) jx += R(cx(q)) * t[p];
-    if (cy(q)) jy += R(cy(q)) * t[p];
-    if (cz(q)) jz += R(cz(q)) * t[p];
-  }
+  // Everything below the populations is formed from the nine +/- pairs: the
+  // axis pairs (sum sA, difference tA) and, in each coordinate plane, the
+  // two diagonal pairs P (e_i e_j = +1) and M (e_i e_j = -1), whose sums and
+  // differences give that plane's moments directly, e.g. in the xy plane
+  //   D_xxyy = sP + sM, D_xy = sP - sM, D_xyy = tP + tM, D_xxy = tP - tM.
+  static_assert(opp(1) == 2 && opp(3) == 4 && opp(5) == 6 && opp(7) == 10 && opp(9) == 8 &&
+                    opp(11) == 14 && opp(13) == 12 && opp(15) == 18 && opp(17) == 16,
+                "pair layout");
+  static_assert(cx(1) == 1 && cy(3) == 1 && cz(5) == 1 && cx(7) == 1 && cy(7) == 1 &&
+                    cx(9) == 1 && cy(9) == -1 && cx(11) == 1 && cz(11) == 1 && cx(13) == 1 &&
+                    cz(13) == -1 && cy(15) == 1 && cz(15) == 1 && cy(17) == 1 && cz(17) == -1,
+                "pair members");
+  R sAx, sAy, sAz, tAx, tAy, tAz;
+  R Dxy, Dxz, Dyz, Dxyy, Dxzz, Dxxy, Dyzz, Dxxz, Dyyz, Dxxyy, Dxxzz, Dyyzz;
+  auto pair_moments = [&]() {
+    sAx = d[1] + d[2];
+    tAx = d[1] - d[2];
+    sAy = d[3] + d[4];
+    tAy = d[3] - d[4];
+    sAz = d[5] + d[6];
+    tAz = d[5] - d[6];
+    {
+      const R sP = d[7] + d[10], tP = d[7] - d[10], sM = d[9] + d[8], tM = d[9] - d[8];
+      Dxxyy = sP + sM;
+      Dxy = sP - sM;
+      Dxyy = tP + tM;
+      Dxxy = tP - tM;
+    }
+    {
+      const R sP = d[11] + d[14], tP = d[11] - d[14], sM = d[13] + d[12], tM = d[13] - d[12];
+      Dxxzz = sP + sM;
+      Dxz = sP - sM;
+      Dxzz = tP + tM;
+      Dxxz = tP - tM;
+    }
+    {
+      const R sP = d[15] + d[18], tP = d[15] - d[18], sM = d[17] + d[16], tM = d[17] - d[16];
+      Dyyzz = sP + sM;
+      Dyz = sP - sM;
+      Dyzz = tP + tM;
+      Dyyz = tP - tM;
+    }
+  };
+  pair_moments();
+  const R drho = d[0] + (sAx + sAy + sAz) + (Dxxyy + Dxxzz + Dyyzz);
+  const R jx = tAx + (Dxyy + Dxzz), jy = tAy + (Dxxy + Dyzz), jz = tAz + (Dxxz + Dyyz);
   const R rho = R(C.rho0) + drho;
   const R rinv = rrcp<R>(rho);
   R ux, uy, uz;
@@ -221,38 +251,12 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
       Sa[q] = R(wt<T>(q)) * (R(T(3) * eF) + R(T(9) * eF) * eu - R(3) * uF);
       d[q] += R(0.5) * Sa[q];
     }
-#pragma unroll
-    for (int p = 0; p < NPAIR; ++p) {
-      s[p] = d[pair_pos(p)] + d[opp(pair_pos(p))];
-      t[p] = d[pair_pos(p)] - d[opp(pair_pos(p))];
-    }
+    pair_moments();
   }
 
   // ---- raw moments of the deviations (Eq. rawmomentdistributionfunction1)
   // k'_ii = rho0/3 + Dii, k'_ij = Dij, third order k' = D, k'_iijj = rho0/9 + D.
-  R Dxx = 0, Dyy = 0, Dzz = 0, Dxy = 0, Dxz = 0, Dyz = 0;
-  R Dxyy = 0, Dxzz = 0, Dxxy = 0, Dyzz = 0, Dxxz = 0, Dyyz = 0;
-  R Dxxyy = 0, Dxxzz = 0, Dyyzz = 0;
-#pragma unroll
-  for (int p = 0; p < NPAIR; ++p) {
-    const int q = pair_pos(p);
-    const int x = cx(q), y = cy(q), z = cz(q);
-    if (x * x) Dxx += s[p];
-    if (y * y) Dyy += s[p];
-    if (z * z) Dzz += s[p];
-    if (x * y) Dxy += R(x * y) * s[p];
-    if (x * z) Dxz += R(x * z) * s[p];
-    if (y * z) Dyz += R(y * z) * s[p];
-    if (x * y * y) Dxyy += R(x * y * y) * t[p];
-    if (x * z * z) Dxzz += R(x * z * z) * t[p];
-    if (x * x * y) Dxxy += R(x * x * y) * t[p];
-    if (y * z * z) Dyzz += R(y * z * z) * t[p];
-    if (x * x * z) Dxxz += R(x * x * z) * t[p];
-    if (y * y * z) Dyyz += R(y * y * z) * t[p];
-    if (x * x * y * y) Dxxyy += s[p];
-    if (x * x * z * z) Dxxzz += s[p];
-    if (y * y * z * z) Dyyzz += s[p];
-  }
+  const R Dxx = sAx + (Dxxyy + Dxxzz), Dyy = sAy + (Dxxyy + Dyyzz), Dzz = sAz + (Dxxzz + Dyyzz);
 
   const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
   const R r3 = R(C.rho0 * T(1.0 / 3.0));
@@ -316,37 +320,39 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
   const R ay = Dyy - third * drho - rho * uy2 - R(6) * g7 + R(6) * g8 + R(42) * g9;
   const R az = Dzz - third * drho - rho * uz2 - R(12) * g8 + R(42) * g9;
 
-  const R b16 = third * drho - (Dxxyy + Dxxzz + Dyyzz) + R(2.0 / 3.0) * (ax + ay + az) +
-                (ax * ay + ax * az + ay * az) * rinv + R(2) * ux * (Dxyy + Dxzz) +
-                R(2) * uy * (Dxxy + Dyzz) + R(2) * uz * (Dxxz + Dyyz) - ux2 * (kyy + kzz) -
-                uy2 * (kzz + kxx) - uz2 * (kxx + kyy) -
-                R(4) * (ux * uy * Dxy + ux * uz * Dxz + uy * uz * Dyz) +
-                R(3) * rho * (ux2 * uy2 + ux2 * uz2 + uy2 * uz2);
-  const R g16 = R(1.0 / 12.0) * b16 - R(4.0 / 3.0) * (ux * uy * g4 + ux * uz * g5 + uy * uz * g6) +
+  // The brackets b16..b18 of g^_16..18 are sums over the axis pairs (xy, xz,
+  // yz) of one pair term each, e.g.
+  //   Wxy = ax ay / rho - k'xxyy + 2 ux k'xyy + 2 uy k'xxy - ux^2 k'yy
+  //         - uy^2 k'xx - 4 ux uy k'xy + 3 rho ux^2 uy^2,
+  // with b16 = rho/3 - rho0/3 + 2/3 (ax + ay + az) + Wxy + Wxz + Wyz,
+  // b17 = (2 ax - ay - az)/3 + Wxy + Wxz - 2 Wyz and b18 = (ay - az)/3 + Wxy - Wxz.
+  const R uxy = ux * uy, uxz = ux * uz, uyz = uy * uz;
+  const R rho3 = R(3) * rho;
+  const R axr = ax * rinv, ayr = ay * rinv;
+  const R Wxy = axr * ay - Dxxyy + tux * Dxyy + tuy * Dxxy - ux2 * kyy - uy2 * kxx -
+                R(4) * uxy * Dxy + rho3 * (ux2 * uy2);
+  const R Wxz = axr * az - Dxxzz + tux * Dxzz + tuz * Dxxz - ux2 * kzz - uz2 * kxx -
+                R(4) * uxz * Dxz + rho3 * (ux2 * uz2);
+  const R Wyz = ayr * az - Dyyzz + tuy * Dyzz + tuz * Dyyz - uy2 * kzz - uz2 * kyy -
+                R(4) * uyz * Dyz + rho3 * (uy2 * uz2);
+  const R b16 = third * drho + R(2.0 / 3.0) * (ax + ay + az) + (Wxy + Wxz + Wyz);
+  const R b17 = third * (R(2) * ax - ay - az) + (Wxy + Wxz) - R(2) * Wyz;
+  const R b18 = third * (ay - az) + (Wxy - Wxz);
+  // shared products: ux uy g4, ux uz g5, uy uz g6 and ux g10, uy g11, uz g12
+  const R p4 = ux * a4y, p5 = ux * a5z, p6 = uy * a6z;
+  const R v10 = ux * g10, v11 = uy * g11, v12 = uz * g12;
+  const R g16 = R(1.0 / 12.0) * b16 - R(4.0 / 3.0) * (p4 + p5 + p6) +
                 R(0.5) * (ux2 - uy2) * g7 + R(0.5) * (ux2 + uy2 - R(2) * uz2) * g8 +
-                (R(-7) * (ux2 + uy2 + uz2) - R(8)) * g9 +
-                R(4.0 / 3.0) * (ux * g10 + uy * g11 + uz * g12);
-
-  const R b17 = -(Dxxyy + Dxxzz - R(2) * Dyyzz) + third * (R(2) * ax - ay - az) +
-                (ax * ay + ax * az - R(2) * ay * az) * rinv +
-                R(2) * ((ux * Dxyy + ux * Dxzz + uy * Dxxy + uz * Dxxz) - R(2) * (uy * Dyzz + uz * Dyyz)) -
-                ux2 * (kyy + kzz) - uy2 * (kxx - R(2) * kzz) - uz2 * (kxx - R(2) * kyy) -
-                R(4) * (ux * uy * Dxy + ux * uz * Dxz - R(2) * uy * uz * Dyz) +
-                R(3) * rho * (ux2 * uy2 + ux2 * uz2 - R(2) * uy2 * uz2);
-  const R g17 = R(1.0 / 24.0) * b17 - R(2.0 / 3.0) * (ux * uy * g4 + ux * uz * g5) +
-                R(4.0 / 3.0) * uy * uz * g6 + R(0.25) * (ux2 - uy2 - R(3) * uz2 - R(2)) * g7 +
+                (R(-7) * (ux2 + uy2 + uz2) - R(8)) * g9 + R(4.0 / 3.0) * (v10 + v11 + v12);
+  const R g17 = R(1.0 / 24.0) * b17 - R(2.0 / 3.0) * (p4 + p5) + R(4.0 / 3.0) * p6 +
+                R(0.25) * (ux2 - uy2 - R(3) * uz2 - R(2)) * g7 +
                 R(0.25) * (ux2 - R(5) * uy2 + uz2 - R(2)) * g8 +
-                R(1.75) * (R(-2) * ux2 + uy2 + uz2) * g9 + R(2.0 / 3.0) * ux * g10 -
-                third * (uy * g11 + uz * g12) - uy * g14 + uz * g15;
-
-  const R b18 = -(Dxxyy - Dxxzz) + third * (ay - az) + ax * (ay - az) * rinv +
-                R(2) * (ux * (Dxyy - Dxzz) + uy * Dxxy - uz * Dxxz) - ux2 * (Dyy - Dzz) +
-                (uz2 - uy2) * kxx - R(4) * (ux * uy * Dxy - ux * uz * Dxz) +
-                R(3) * rho * (ux2 * uy2 - ux2 * uz2);
-  const R g18 = R(0.125) * b18 - R(2) * ux * uy * g4 + R(2) * ux * uz * g5 +
+                R(1.75) * (R(-2) * ux2 + uy2 + uz2) * g9 + R(2.0 / 3.0) * v10 -
+                third * (v11 + v12) - uy * g14 + uz * g15;
+  const R g18 = R(0.125) * b18 - R(2) * (p4 - p5) +
                 R(0.75) * (ux2 - uy2 + uz2 + R(2.0 / 3.0)) * g7 +
                 R(0.75) * (R(-3) * ux2 - uy2 + uz2 - R(2)) * g8 + R(5.25) * (uz2 - uy2) * g9 +
-                uy * g11 - uz * g12 + R(2) * ux * g13 - uy * g14 - uz * g15;
+                (v11 - v12) + R(2) * ux * g13 - uy * g14 - uz * g15;
 
   // ---- back-transform f~ = f + K g^ (+ second half of the source) --------
   // Columns of K grouped by velocity class (Sec. 2, the basis vectors): the
