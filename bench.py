@@ -415,22 +415,20 @@ def _batch_bench(clbm, torch, wl, steps, peak):
             "timing": "host wall clock around graph-captured batch steps, synchronised"}
 
 
-def _serving_bench(clbm, wl, n_req, seq_req):
-    """Poisson trace through the continuous-batching server (FP16S), and the
-    first requests solved one at a time by the plain FP64 solver."""
-    trace = wl.serving_trace(count=n_req, seed=0, rate=20.0, cavity_L=(16, 48),
-                             channel_H=(16, 64), Re_range=(50.0, 400.0))
-    tol, cap, plateau = 1e-7, 200_000, 20
-    with clbm.Server("f16s", hbm_budget_bytes=150e9, max_active=64, check_interval=100) as srv:
+def _serve_trace(clbm, trace, dtype, tol, cap, plateau, keep):
+    """Replay the trace through the continuous-batching server; the first
+    `keep` requests keep their fields."""
+    with clbm.Server(dtype, hbm_budget_bytes=150e9, max_active=64, check_interval=100) as srv:
         t0 = time.perf_counter()
         ids = []
-        for r in trace:
+        for k, r in enumerate(trace):
             delay = t0 + r.arrival - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
             ids.append(srv.submit(**r.problem.kwargs(), tol=tol, max_steps=cap,
-                                  plateau_checks=plateau))
+                                  plateau_checks=plateau, keep_fields=k < keep))
         res = [srv.wait(i) for i in ids]
+        fields = [srv.fields(i) for i in ids[:keep]]
         info = srv.info()
     lat = sorted(r["t_done"] - r["t_submit"] for r in res)
     span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
@@ -438,37 +436,96 @@ def _serving_bench(clbm, wl, n_req, seq_req):
     for r in res:
         k = clbm.SOLVE_STATUS[r["status"]]
         status[k] = status.get(k, 0) + 1
-    # sequential FP64 baseline on the first requests
+    q = lambda p: lat[min(len(lat) - 1, int(round(p * (len(lat) - 1))))]
+    out = {"form": dtype, "solves_per_s": len(res) / span, "p50_latency_s": q(0.5),
+           "p99_latency_s": q(0.99), "makespan_s": span, "status": status,
+           "mean_steps": sum(r["steps"] for r in res) / len(res),
+           "server_MLUPS": info["lattice_updates"] / max(info["busy_seconds"], 1e-9) / 1e6}
+    return out, res, fields
+
+
+def _serving_bench(clbm, wl, n_req, seq_req):
+    """Poisson trace through the continuous-batching server in three storage
+    forms (F16R, F16S, FP32), and the first requests solved one at a time by
+    the plain FP64 solver (the solves/s baseline).  Each served result of
+    those requests is compared with FP64 after the same number of steps."""
+    import numpy as np
+    trace = wl.serving_trace(count=n_req, seed=0, rate=20.0, cavity_L=(16, 48),
+                             channel_H=(16, 64), Re_range=(50.0, 400.0))
+    tol, cap, plateau = 1e-7, 200_000, 20
+    forms, kept = {}, {}
+    for dt in ("f16r", "f16s", "f32"):
+        forms[dt], res, fields = _serve_trace(clbm, trace, dt, tol, cap, plateau, seq_req)
+        kept[dt] = (res, fields)
+    # sequential FP64 on the first requests: baseline and reference velocities
     t0 = time.perf_counter()
-    seq_steps = []
+    ref = []
     for r in trace[:seq_req]:
         with clbm.Lattice(**r.problem.kwargs(), dtype="f64", check_interval=100) as lt:
-            best, since, steps = float("inf"), 0, 0
+            best, since, steps, status = float("inf"), 0, 0, "max_steps"
             while steps < cap:
                 lt.step(100)
                 steps += 100
                 R, rc = lt.residual()
-                if rc != 0 or R <= tol:
+                if rc != 0:
+                    status = "diverged"
+                    break
+                if R <= tol:
+                    status = "converged"
                     break
                 if R < 0.9 * best:
                     best, since = R, 0
                 elif R == R and R != float("inf"):
                     since += 1
                 if since >= plateau:
+                    status = "plateau"
                     break
-            seq_steps.append(steps)
+            ref.append((status, steps))
     seq_dt = time.perf_counter() - t0
-    q = lambda p: lat[min(len(lat) - 1, int(round(p * (len(lat) - 1))))]
-    return {"workload": f"{n_req} requests, Poisson 20/s (seed 0), half cavities L~U{{16..48}}, "
-                        "half channels 8xU{16..64}x8, Re~U[50,400], n~U[0.4,1.6], FP16S, "
-                        f"tol {tol}, cap {cap} steps, plateau {plateau} checks",
-            "solves_per_s": len(res) / span, "p50_latency_s": q(0.5), "p99_latency_s": q(0.99),
-            "makespan_s": span, "status": status,
-            "mean_steps": sum(r["steps"] for r in res) / len(res),
-            "server_MLUPS": info["lattice_updates"] / max(info["busy_seconds"], 1e-9) / 1e6,
-            "sequential_f64_solves_per_s": seq_req / seq_dt,
-            "sequential_f64_sample": f"first {seq_req} requests one at a time, plain FP64 "
-                                     f"handles, mean {sum(seq_steps) / len(seq_steps):.0f} steps"}
+    # accuracy: each served result against FP64 after the same number of
+    # steps (one untimed FP64 run per request, sampled at each form's count)
+    bars = {"f16r": 2e-3, "f16s": 2e-3, "f32": 1e-4}
+    l2 = {dt: [] for dt in forms}
+    for k, r in enumerate(trace[:seq_req]):
+        want = sorted({kept[dt][0][k]["steps"] for dt in forms
+                       if clbm.SOLVE_STATUS[kept[dt][0][k]["status"]] != "diverged"})
+        if not want:
+            continue
+        u64 = {}
+        try:
+            with clbm.Lattice(**r.problem.kwargs(), dtype="f64", check_interval=100) as lt:
+                done = 0
+                for n in want:
+                    lt.step(n - done)
+                    done = n
+                    u64[n] = lt.fields()[1]
+        except clbm.CLBMError:
+            pass   # FP64 diverged first: only the counts reached so far are compared
+        for dt in forms:
+            res, fields = kept[dt]
+            if res[k]["steps"] in u64:
+                ref_u = u64[res[k]["steps"]]
+                l2[dt].append(float(np.linalg.norm(fields[k][1] - ref_u) / np.linalg.norm(ref_u)))
+    for dt, out in forms.items():
+        out["velocity_l2_vs_f64"] = l2[dt]
+        out["within_bar"] = f"{sum(x <= bars[dt] for x in l2[dt])}/{len(l2[dt])} at L2 <= {bars[dt]:g}"
+    head = forms["f16r"]
+    head.update({
+        "workload": f"{n_req} requests, Poisson 20/s (seed 0), half cavities L~U{{16..48}}, "
+                    "half channels 8xU{16..64}x8, Re~U[50,400], n~U[0.4,1.6], FP32 math, "
+                    f"tol {tol}, cap {cap} steps, plateau {plateau} checks",
+        "accuracy_sample": f"velocity L2 of each served result (first {seq_req} requests, not "
+                           "diverged) against the same request stepped in FP64 for the same "
+                           "number of steps",
+        "other_forms": {dt: {k: forms[dt][k] for k in ("solves_per_s", "p50_latency_s",
+                                                       "p99_latency_s", "status",
+                                                       "velocity_l2_vs_f64", "within_bar")}
+                        for dt in ("f16s", "f32")},
+        "sequential_f64_solves_per_s": seq_req / seq_dt,
+        "sequential_f64_sample": f"first {seq_req} requests one at a time, plain FP64 handles, "
+                                 f"statuses {[st for st, _ in ref]}, "
+                                 f"mean {sum(n for _, n in ref) / len(ref):.0f} steps"})
+    return head
 
 
 def _run_to_steady(clbm, prob, dtype, tol, max_steps, plateau=20, chunk=1000):
@@ -608,7 +665,7 @@ def main():
                     help="skip the batched and serving measurements")
     ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--serve-requests", type=int, default=48)
-    ap.add_argument("--serve-seq", type=int, default=4)
+    ap.add_argument("--serve-seq", type=int, default=8)
     ap.add_argument("--precision", action="store_true",
                     help="velocity error of the FP32 / F16S forms against FP64")
     ap.add_argument("--precision-steps", type=int, default=2000)

@@ -177,7 +177,7 @@ int clbm_set_launch(clbm_handle h, int block_x, int block_y, int npt);
 
 /* ---- Batched stepping of many lattices --------------------------------
  * Not in the paper: a batch steps up to `capacity` lattices of one storage
- * form together, one launch of a persistent kernel per time step for all of
+ * form (any of the four, F16R with its reference moments) together, one launch of a persistent kernel per time step for all of
  * them (tiles of every lattice from a device-side table), with each whole
  * check interval queued as one CUDA graph.  Lattices join and leave between
  * clbm_batch_step() calls; each keeps its own buffers, parameters, step

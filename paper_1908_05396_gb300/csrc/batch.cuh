@@ -18,6 +18,7 @@ namespace clbm {
 template <typename R>
 struct LatDesc {
   const void* buf[2];  // buf[p]: source buffer at parity p (the other is the destination)
+  const void* ref[2];  // F16R form: the reference moments kept with buf[p] (else null)
   void* uprev;         // velocities of the previous check (math type)
   int64_t qstride;
   int nx, ny, nz, pitch, plane;
@@ -71,6 +72,12 @@ __device__ __forceinline__ void batch_node(const LatDesc<R>& L, const S* __restr
   for (int q = 0; q < Q; ++q) dst[q * qs + i] = Codec<S, R>::enc(d[q], R(1));
 }
 
+// One node of the batched step in the F16R form (defined with the other F16R
+// kernels, the only translation unit that instantiates the batch with REF).
+template <bool FORCE>
+__device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y, int z,
+                               NodeOut<float>& o);
+
 // tile word: x tile (8 bits) | y tile (12 bits) | z chunk (12 bits)
 __host__ __device__ __forceinline__ unsigned tile_word(int tx, int ty, int tz) {
   return unsigned(tx) | (unsigned(ty) << 8) | (unsigned(tz) << 20);
@@ -79,7 +86,7 @@ __host__ __device__ __forceinline__ unsigned tile_word(int tx, int ty, int tz) {
 // The tile loop of the batched step.  get(li) returns lattice li's
 // descriptor from the translation unit's __constant__ table, so ptxas can
 // reload its fields where it needs them instead of holding them in registers.
-template <typename S, typename R, bool CHECK, bool FORCE, typename Get>
+template <typename S, typename R, bool CHECK, bool FORCE, bool REF, typename Get>
 __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ owner,
                                             const unsigned* __restrict__ coord,
                                             BatchHeader* hdr, int parity, double* acc) {
@@ -87,9 +94,18 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
   const int t0 = FORCE ? hdr->ntiles0 : 0;
   const int t1 = FORCE ? hdr->ntiles : hdr->ntiles0;
   const int nlat = hdr->nlat;
-  for (int t = t0 + int(blockIdx.x); t < t1; t += gridDim.x) {
-    const int li = owner[t];
-    const unsigned w = coord[t];
+  // The next tile's table entries are loaded while this tile collides, so a
+  // tile starts with one dependent round trip (descriptor) instead of two.
+  int t = t0 + int(blockIdx.x);
+  int li_next = t < t1 ? owner[t] : 0;
+  unsigned w_next = t < t1 ? coord[t] : 0u;
+  for (; t < t1; t += gridDim.x) {
+    const int li = li_next;
+    const unsigned w = w_next;
+    if (t + int(gridDim.x) < t1) {
+      li_next = owner[t + gridDim.x];
+      w_next = coord[t + gridDim.x];
+    }
     const int tx = int(w & 0xffu), ty = int((w >> 8) & 0xfffu), tz = int(w >> 20);
     // Self-check of the tables before any access through them.
     bool ok = li >= 0 && li < nlat;
@@ -98,7 +114,7 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
       ok = L.buf[0] != nullptr && L.buf[1] != nullptr && tx < L.tiles_x && ty < L.tiles_y &&
            tz < L.nz && L.pitch >= L.nx && L.plane == L.pitch * L.ny &&
            L.qstride >= int64_t(L.plane) * L.nz && 19 * L.qstride < (int64_t(1) << 31) &&
-           (L.C.has_force != 0) == FORCE;
+           (L.C.has_force != 0) == FORCE && (!REF || (L.ref[0] != nullptr && L.ref[1] != nullptr));
     if (!ok) {  // block-uniform: skip the tile, report it
       if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(&hdr->err, 1);
       continue;
@@ -114,7 +130,8 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
     if (active) {
       {
         NodeOut<R> o;
-        batch_node<S, R, FORCE>(L, src, dst, x, y, z, o);
+        if constexpr (REF) batch_node_ref<FORCE>(L, parity, x, y, z, o);
+        else batch_node<S, R, FORCE>(L, src, dst, x, y, z, o);
         if (CHECK) {
           R* up = static_cast<R*>(L.uprev);
           const int64_t nst = int64_t(L.plane) * L.nz;
@@ -154,10 +171,13 @@ constexpr int BATCH_CONST_BYTES = 60 * 1024;
 // Host-side fill of one descriptor (constants converted once, in double).
 template <typename R>
 void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur, const void* other,
-                 void* uprev, int tiles_x, int tiles_y, int tile_begin, int slot) {
+                 const void* ref_cur, const void* ref_other, void* uprev, int tiles_x,
+                 int tiles_y, int tile_begin, int slot) {
   LatDesc<R> L{};
   L.buf[0] = cur;
   L.buf[1] = other;
+  L.ref[0] = ref_cur;
+  L.ref[1] = ref_other;
   L.uprev = uprev;
   L.qstride = g.qstride;
   L.nx = g.nx;
@@ -179,7 +199,7 @@ void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur,
 
 }  // namespace clbm
 
-#define CLBM_DEFINE_BATCH(SUFFIX, S, R)                                                        \
+#define CLBM_DEFINE_BATCH(SUFFIX, S, R, REF)                                                   \
   namespace clbm {                                                                             \
   __constant__ LatDesc<R> c_lat_##SUFFIX[BATCH_CONST_BYTES / sizeof(LatDesc<R>)];              \
   template <bool CHECK, bool CAP, bool FORCE>                                                  \
@@ -187,7 +207,7 @@ void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur,
       batch_kernel_##SUFFIX(int base, const int* __restrict__ owner,                           \
                             const unsigned* __restrict__ coord, BatchHeader* hdr, int parity,  \
                             double* acc) {                                                     \
-    batch_tiles<S, R, CHECK, FORCE>(                                                           \
+    batch_tiles<S, R, CHECK, FORCE, REF>(                                                      \
         [base](int li) -> const LatDesc<R>& { return c_lat_##SUFFIX[base + li]; }, owner,      \
         coord, hdr, parity, acc);                                                              \
   }                                                                                            \
@@ -220,8 +240,9 @@ void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur,
   size_t desc_size_##SUFFIX() { return sizeof(LatDesc<R>); }                                    \
   int desc_capacity_##SUFFIX() { return int(BATCH_CONST_BYTES / sizeof(LatDesc<R>)); }         \
   void fill_desc_##SUFFIX(void* out, const Geom& g, const PhysParams& P, const void* cur,        \
-                          const void* other, void* uprev, int tx, int ty, int tb, int slot) {  \
-    fill_desc_t<R>(out, g, P, cur, other, uprev, tx, ty, tb, slot);                            \
+                          const void* other, const void* ref_cur, const void* ref_other,       \
+                          void* uprev, int tx, int ty, int tb, int slot) {                     \
+    fill_desc_t<R>(out, g, P, cur, other, ref_cur, ref_other, uprev, tx, ty, tb, slot);        \
   }                                                                                            \
   cudaError_t upload_desc_##SUFFIX(const void* host, int base, int n) {                        \
     return cudaMemcpyToSymbol(c_lat_##SUFFIX, host, size_t(n) * sizeof(LatDesc<R>),            \

@@ -77,16 +77,21 @@ int bfail(clbm_batch_ctx* b, int code, const std::string& m) {
   } while (0)
 
 size_t desc_size(clbm_dtype t) {
-  return t == CLBM_F64 ? desc_size_f64() : t == CLBM_F32 ? desc_size_f32() : desc_size_f16();
+  return t == CLBM_F64   ? desc_size_f64()
+         : t == CLBM_F32 ? desc_size_f32()
+         : t == CLBM_F16R ? desc_size_f16r()
+                          : desc_size_f16();
 }
 
 // Ranges of the per-form __constant__ descriptor tables held by live batches.
 std::mutex g_table_mu;
-std::vector<std::pair<int, int>> g_table_used[3];  // (base, count) per dtype
+std::vector<std::pair<int, int>> g_table_used[4];  // (base, count) per dtype
 
 int table_capacity(clbm_dtype t) {
-  return t == CLBM_F64 ? desc_capacity_f64() : t == CLBM_F32 ? desc_capacity_f32()
-                                                             : desc_capacity_f16();
+  return t == CLBM_F64    ? desc_capacity_f64()
+         : t == CLBM_F32  ? desc_capacity_f32()
+         : t == CLBM_F16R ? desc_capacity_f16r()
+                          : desc_capacity_f16();
 }
 
 int table_reserve(clbm_dtype t, int n) {
@@ -114,17 +119,26 @@ void table_release(clbm_dtype t, int base) {
 }
 
 cudaError_t upload_desc(clbm_dtype t, const void* host, int base, int n) {
-  return t == CLBM_F64 ? upload_desc_f64(host, base, n)
-         : t == CLBM_F32 ? upload_desc_f32(host, base, n)
-                         : upload_desc_f16(host, base, n);
+  return t == CLBM_F64    ? upload_desc_f64(host, base, n)
+         : t == CLBM_F32  ? upload_desc_f32(host, base, n)
+         : t == CLBM_F16R ? upload_desc_f16r(host, base, n)
+                          : upload_desc_f16(host, base, n);
 }
 
 void fill_desc(clbm_dtype t, void* out, const clbm_ctx* h, int tx, int ty, int tb, int slot) {
   const void* cur = h->buf[h->cur];
   const void* other = h->buf[1 - h->cur];
-  if (t == CLBM_F64) fill_desc_f64(out, h->g, h->P, cur, other, h->uprev, tx, ty, tb, slot);
-  else if (t == CLBM_F32) fill_desc_f32(out, h->g, h->P, cur, other, h->uprev, tx, ty, tb, slot);
-  else fill_desc_f16(out, h->g, h->P, cur, other, h->uprev, tx, ty, tb, slot);
+  // F16R: the reference moments travel with their population buffers
+  const void* rcur = h->ref[h->cur];
+  const void* rother = h->ref[1 - h->cur];
+  if (t == CLBM_F64)
+    fill_desc_f64(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot);
+  else if (t == CLBM_F32)
+    fill_desc_f32(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot);
+  else if (t == CLBM_F16R)
+    fill_desc_f16r(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot);
+  else
+    fill_desc_f16(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot);
 }
 
 cudaError_t launch(clbm_batch_ctx* b, bool check) {
@@ -136,6 +150,9 @@ cudaError_t launch(clbm_batch_ctx* b, bool check) {
     case CLBM_F32:
       return launch_batch_f32(b->desc_base, b->d_owner, b->d_coord, b->d_hdr, b->parity, check,
                               b->d_acc, b->block, grid, b->stream);
+    case CLBM_F16R:
+      return launch_batch_f16r(b->desc_base, b->d_owner, b->d_coord, b->d_hdr, b->parity, check,
+                               b->d_acc, b->block, grid, b->stream);
     default:
       return launch_batch_f16(b->desc_base, b->d_owner, b->d_coord, b->d_hdr, b->parity, check,
                               b->d_acc, b->block, grid, b->stream);
@@ -278,9 +295,7 @@ int clbm_batch_create(clbm_dtype dtype, int capacity, int check_interval, void* 
                       clbm_batch* out) {
   if (!out) return bfail(nullptr, CLBM_ERR_ARG, "null output");
   *out = nullptr;
-  if (dtype == CLBM_F16R)
-    return bfail(nullptr, CLBM_ERR_UNSUPPORTED, "the batched step does not take the F16R form");
-  if (dtype != CLBM_F64 && dtype != CLBM_F32 && dtype != CLBM_F16S)
+  if (dtype != CLBM_F64 && dtype != CLBM_F32 && dtype != CLBM_F16S && dtype != CLBM_F16R)
     return bfail(nullptr, CLBM_ERR_ARG, "unknown dtype");
   if (capacity < 1 || capacity > (1 << 16)) return bfail(nullptr, CLBM_ERR_ARG, "capacity must be in [1, 65536]");
   if (check_interval <= 0) check_interval = 100;
@@ -441,9 +456,13 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
     clbm_ctx* h = b->slots[s];
     if (!h) continue;
     const size_t bytes = size_t(NQ) * size_t(h->g.qstride) * h->elem;
-    err = cudaMallocAsync(&saved[s], bytes, b->stream);
+    const size_t rbytes = h->ref[0] ? (size_t(h->g.plane) * h->g.nz + 64) * 8 : 0;
+    err = cudaMallocAsync(&saved[s], bytes + rbytes, b->stream);
     if (err == cudaSuccess)
       err = cudaMemcpyAsync(saved[s], h->buf[h->cur], bytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (err == cudaSuccess && rbytes)
+      err = cudaMemcpyAsync(static_cast<char*>(saved[s]) + bytes, h->ref[h->cur], rbytes,
+                            cudaMemcpyDeviceToDevice, b->stream);
     cur0[s] = h->cur;
     steps0[s] = h->steps;
   }
@@ -503,8 +522,12 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
     h->cur = cur0[s];
     h->steps = steps0[s];
     const size_t bytes = size_t(NQ) * size_t(h->g.qstride) * h->elem;
+    const size_t rbytes = h->ref[0] ? (size_t(h->g.plane) * h->g.nz + 64) * 8 : 0;
     cudaError_t e2 = cudaMemcpyAsync(h->buf[h->cur], saved[s], bytes, cudaMemcpyDeviceToDevice,
                                      b->stream);
+    if (e2 == cudaSuccess && rbytes)
+      e2 = cudaMemcpyAsync(h->ref[h->cur], static_cast<char*>(saved[s]) + bytes, rbytes,
+                           cudaMemcpyDeviceToDevice, b->stream);
     if (err == cudaSuccess) err = e2;
     cudaFreeAsync(saved[s], b->stream);
   }

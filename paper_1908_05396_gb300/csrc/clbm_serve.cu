@@ -93,7 +93,8 @@ int sfail(clbm_server_ctx* s, int code, const std::string& m) {
 }
 
 // Device bytes of one lattice of this form (two population buffers, the
-// check velocities, small work buffers), with the library's padding.
+// check velocities, the F16R reference moments, small work buffers), with the
+// library's padding.
 double lattice_bytes(clbm_dtype t, const clbm_domain& d) {
   const int64_t elem = t == CLBM_F64 ? 8 : t == CLBM_F32 ? 4 : 2;
   const int64_t rs = t == CLBM_F64 ? 8 : 4;
@@ -101,7 +102,8 @@ double lattice_bytes(clbm_dtype t, const clbm_domain& d) {
   const int64_t pitch = (d.nx + per_row - 1) / per_row * per_row;
   const int64_t plane = pitch * d.ny;
   const int64_t qs = (plane * d.nz + 255) / 256 * 256;
-  return double(2 * 19 * qs * elem + 3 * plane * d.nz * rs + 4096);
+  const int64_t refs = t == CLBM_F16R ? 2 * (plane * d.nz + 64) * 8 : 0;  // F16R references
+  return double(2 * 19 * qs * elem + 3 * plane * d.nz * rs + refs + 4096);
 }
 
 void finish(clbm_server_ctx* s, Active& a, int status, double R, double mass, int64_t steps) {

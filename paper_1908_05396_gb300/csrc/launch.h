@@ -89,10 +89,12 @@ struct BatchHeader {
   int desc_capacity_##SUFFIX();                                                                 \
   cudaError_t upload_desc_##SUFFIX(const void* host, int base, int n);                          \
   void fill_desc_##SUFFIX(void* out, const Geom& g, const PhysParams& P, const void* cur,       \
-                          const void* other, void* uprev, int tx, int ty, int tb, int slot);
+                          const void* other, const void* ref_cur, const void* ref_other,      \
+                          void* uprev, int tx, int ty, int tb, int slot);
 CLBM_DECLARE_BATCH(f64)
 CLBM_DECLARE_BATCH(f32)
 CLBM_DECLARE_BATCH(f16)
+CLBM_DECLARE_BATCH(f16r)
 
 // F16R form (step_f16r.cu): FP16 populations relative to each node's stored
 // first-order equilibrium reference.

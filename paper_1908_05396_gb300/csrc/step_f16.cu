@@ -3,4 +3,4 @@
 #include "kernels.cuh"
 
 CLBM_DEFINE_LAUNCHERS(f16, __half, float)
-CLBM_DEFINE_BATCH(f16, __half, float)
+CLBM_DEFINE_BATCH(f16, __half, float, false)

@@ -12,7 +12,7 @@
 // the reference exactly as stored (rounded to FP16), so the encoding is
 // exactly invertible up to the FP16 rounding of the small remainder.
 // The reference arrays are double-buffered with the populations.
-#include "kernels.cuh"
+#include "batch.cuh"
 
 namespace clbm {
 namespace {
@@ -54,38 +54,44 @@ struct RefArgs {
   uint2* ref_dst;        // references written by this step
 };
 
-// General pull (y or z face, or any node when `all` paths are wanted):
-// resolves the source like pull_general and decodes with the writer's
-// reference.
-__device__ __noinline__ float pull_general_ref(const __half* __restrict__ src,
-                                               const uint2* __restrict__ ref, int64_t qstride,
-                                               int nx, int ny, int nz, int pitch, int plane,
-                                               unsigned facebits, int q, int x, int y, int z,
-                                               int i, float lid, float rho0) {
-  int s0 = x - cx(q), s1 = y - cy(q), s2 = z - cz(q);
-  bool bounce = false, islid = false;
-  if (s0 < 0 || s0 >= nx) {
-    const int k = (facebits >> (s0 < 0 ? 0 : 2)) & 3;
-    if (k == BC_PERIODIC) s0 += s0 < 0 ? nx : -nx;
-    else { bounce = true; islid = k == BC_LID; }
+// Pull of all 19 directions into node (x, y, z) with index i, for a node on
+// any face, by the face rules of pull_face; each value is decoded with the
+// reference of the node that wrote it: the upwind (or wrapped) node for a
+// streamed value, the node itself for a bounced one.
+__device__ __forceinline__ void pull_face_ref(const __half* __restrict__ src,
+                                              const uint2* __restrict__ ref, int64_t qstride,
+                                              int nx, int ny, int nz, int pitch, int plane,
+                                              unsigned fb, int x, int y, int z, int i,
+                                              const float* lidc, float rho0, float (&d)[Q]) {
+  const bool fx0 = x == 0, fx1 = x == nx - 1, fy0 = y == 0, fy1 = y == ny - 1;
+  const bool fz0 = z == 0, fz1 = z == nz - 1;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const __half* sq = src + int64_t(q) * qstride;
+    const bool ox = (cx(q) == 1 && fx0) || (cx(q) == -1 && fx1);
+    const bool oy = (cy(q) == 1 && fy0) || (cy(q) == -1 && fy1);
+    const bool oz = (cz(q) == 1 && fz0) || (cz(q) == -1 && fz1);
+    const int up = i - (cz(q) * plane + cy(q) * pitch + cx(q));
+    if (!(ox || oy || oz)) {
+      d[q] = dec16(sq[up]) + ref_term(q, ref_load(ref + up), rho0);
+      continue;
+    }
+    const int kx = ox ? int((fb >> (cx(q) == 1 ? 0 : 2)) & 3u) : int(BC_PERIODIC);
+    const int ky = oy ? int((fb >> (cy(q) == 1 ? 4 : 6)) & 3u) : int(BC_PERIODIC);
+    const int kz = oz ? int((fb >> (cz(q) == 1 ? 8 : 10)) & 3u) : int(BC_PERIODIC);
+    if (kx != BC_PERIODIC || ky != BC_PERIODIC || kz != BC_PERIODIC) {
+      const bool lid = kx == BC_LID || ky == BC_LID || kz == BC_LID;
+      const float v = dec16(src[int64_t(opp(q)) * qstride + i]) +
+                      ref_term(opp(q), ref_load(ref + i), rho0);
+      d[q] = lid ? v + lidc[q] : v;
+    } else {
+      int j = up;
+      if (ox) j += cx(q) == 1 ? nx : -nx;
+      if (oy) j += cy(q) == 1 ? ny * pitch : -ny * pitch;
+      if (oz) j += cz(q) == 1 ? nz * plane : -nz * plane;
+      d[q] = dec16(sq[j]) + ref_term(q, ref_load(ref + j), rho0);
+    }
   }
-  if (s1 < 0 || s1 >= ny) {
-    const int k = (facebits >> (s1 < 0 ? 4 : 6)) & 3;
-    if (k == BC_PERIODIC) s1 += s1 < 0 ? ny : -ny;
-    else { bounce = true; islid = islid || k == BC_LID; }
-  }
-  if (s2 < 0 || s2 >= nz) {
-    const int k = (facebits >> (s2 < 0 ? 8 : 10)) & 3;
-    if (k == BC_PERIODIC) s2 += s2 < 0 ? nz : -nz;
-    else { bounce = true; islid = islid || k == BC_LID; }
-  }
-  if (bounce) {
-    const int qb = opp(q);
-    const float v = dec16(src[int64_t(qb) * qstride + i]) + ref_term(qb, ref_load(ref + i), rho0);
-    return islid ? v + lid : v;
-  }
-  const int j = s2 * plane + s1 * pitch + s0;
-  return dec16(src[int64_t(q) * qstride + j]) + ref_term(q, ref_load(ref + j), rho0);
 }
 
 template <bool FORCE, bool CHECK, bool CAP>
@@ -126,10 +132,8 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
         }
       }
     } else {
-#pragma unroll
-      for (int q = 0; q < Q; ++q)
-        d[q] = pull_general_ref(a.src, r.ref_src, a.qstride, a.nx, a.ny, a.nz, a.pitch, a.plane,
-                                a.facebits, q, x, y, z, i, a.lidc[q], rho0);
+      pull_face_ref(a.src, r.ref_src, a.qstride, a.nx, a.ny, a.nz, a.pitch, a.plane, a.facebits,
+                    x, y, z, i, a.lidc, rho0, d);
     }
     NodeOut<float> o;
     collide<float, FORCE>(a.C, d, o);
@@ -174,10 +178,8 @@ __global__ void __launch_bounds__(256) fields_ref_kernel(const __half* __restric
   if (x >= g.nx || y >= g.ny) return;
   const int i = z * int(g.plane) + y * g.pitch + x;
   float d[Q];
-#pragma unroll
-  for (int q = 0; q < Q; ++q)
-    d[q] = pull_general_ref(src, ref, g.qstride, g.nx, g.ny, g.nz, g.pitch, int(g.plane),
-                            g.facebits, q, x, y, z, i, lidc[q], C.rho0);
+  pull_face_ref(src, ref, g.qstride, g.nx, g.ny, g.nz, g.pitch, int(g.plane), g.facebits, x, y,
+                z, i, lidc, C.rho0, d);
   NodeOut<float> o;
   collide<float, FORCE>(C, d, o);
   const int64_t N = int64_t(g.nx) * g.ny * g.nz;
@@ -280,6 +282,53 @@ void lid_table(const Geom& g, float* out) {
 
 }  // namespace
 
+// One node of the batched step in the F16R form: the same pull, references
+// and collision as step_ref_kernel.
+template <bool FORCE>
+__device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y, int z,
+                               NodeOut<float>& o) {
+  const __half* src = static_cast<const __half*>(L.buf[parity]);
+  __half* dst = static_cast<__half*>(const_cast<void*>(L.buf[parity ^ 1]));
+  const uint2* rs = static_cast<const uint2*>(L.ref[parity]);
+  uint2* rd = static_cast<uint2*>(const_cast<void*>(L.ref[parity ^ 1]));
+  const float rho0 = L.C.rho0;
+  const int qs = int(L.qstride), plane = L.plane, pitch = L.pitch;
+  const int i = z * plane + y * pitch + x;
+  float d[Q];
+  if (y > 0 && y < L.ny - 1 && z > 0 && z < L.nz - 1) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int j = i - (cz(q) * plane + cy(q) * pitch + cx(q));
+      d[q] = dec16(src[q * qs + j]) + ref_term(q, ref_load(rs + j), rho0);
+    }
+    if (x == 0 || x == L.nx - 1) {
+      const int kl = L.facebits & 3, kr = (L.facebits >> 2) & 3;
+#pragma unroll
+      for (int q = 1; q < Q; ++q) {
+        const bool left = cx(q) == 1 && x == 0, right = cx(q) == -1 && x == L.nx - 1;
+        if (left || right) {
+          const int k = left ? kl : kr;
+          if (k == BC_PERIODIC) {
+            const int j = i - (cz(q) * plane + cy(q) * pitch + cx(q)) + (left ? L.nx : -L.nx);
+            d[q] = dec16(src[q * qs + j]) + ref_term(q, ref_load(rs + j), rho0);
+          } else {
+            d[q] = dec16(src[opp(q) * qs + i]) + ref_term(opp(q), ref_load(rs + i), rho0) +
+                   (k == BC_LID ? L.lidc[q] : 0.0f);
+          }
+        }
+      }
+    }
+  } else {
+    pull_face_ref(src, rs, L.qstride, L.nx, L.ny, L.nz, pitch, plane, L.facebits, x, y, z, i,
+                  L.lidc, rho0, d);
+  }
+  collide<float, FORCE>(L.C, d, o);
+  Ref4 rr;
+  rd[i] = ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rr);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) dst[q * qs + i] = enc16(d[q] - ref_term(q, rr, rho0));
+}
+
 cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, void* ref_dst,
                              const Geom& g, const PhysParams& P, const CheckBufs& cb, bool check,
                              dim3 block, int npt, cudaStream_t st) {
@@ -381,3 +430,5 @@ cudaError_t launch_collide_nodes_f16r(const PhysParams& P, const double* fin, do
 }
 
 }  // namespace clbm
+
+CLBM_DEFINE_BATCH(f16r, __half, float, true)

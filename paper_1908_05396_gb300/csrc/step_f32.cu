@@ -3,4 +3,4 @@
 #include "kernels.cuh"
 
 CLBM_DEFINE_LAUNCHERS(f32, float, float)
-CLBM_DEFINE_BATCH(f32, float, float)
+CLBM_DEFINE_BATCH(f32, float, float, false)

@@ -3,4 +3,4 @@
 #include "kernels.cuh"
 
 CLBM_DEFINE_LAUNCHERS(f64, double, double)
-CLBM_DEFINE_BATCH(f64, double, double)
+CLBM_DEFINE_BATCH(f64, double, double, false)

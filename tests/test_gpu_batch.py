@@ -6,7 +6,8 @@ of the batch's check steps must match the lone lattices'.
 FP64 results are bitwise identical.  The FP32-math forms agree to FP32
 rounding (nvcc may fuse a different set of multiply-adds in the batch
 kernel's force path): 1e-6 per population for FP32 storage, one FP16 ulp of
-the stored deviation for F16S."""
+the stored deviation for F16S and F16R (whose stored remainder is smaller
+than the deviation)."""
 import numpy as np
 import pytest
 
@@ -50,7 +51,7 @@ def _same(f, f_ref, dtype):
         assert np.all(np.abs(f - f_ref) <= dev * 2.0 ** -10 + 1e-7)
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s", "f16r"])
 def test_batch_equals_alone(clbm, dtype):
     probs = _mix()
     steps = 257                      # graph chunks + single steps + odd count

@@ -1,7 +1,7 @@
 """Continuous-batching server: results are the same alone and in the mix,
 admission respects the memory budget, and unfinished work is cancelled on
 shutdown.  Tolerances are the per-form ones of the parity tests (FP64
-exact, FP32 1e-6 per population-derived field, F16S one FP16 ulp)."""
+exact, FP32 1e-6 per population-derived field, F16S and F16R one FP16 ulp)."""
 import time
 
 import numpy as np
@@ -35,10 +35,10 @@ def _submit(srv, p, tol):
     return srv.submit(**p.kwargs(), tol=tol, max_steps=6000, keep_fields=True)
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s", "f16r"])
 def test_same_result_alone_and_in_the_mix(clbm, dtype):
     probs = _requests()
-    tol = 1e-4 if dtype == "f16s" else 1e-6
+    tol = {"f16s": 1e-4, "f16r": 1e-5}.get(dtype, 1e-6)
     mixed = {}
     with clbm.Server(dtype, hbm_budget_bytes=4e9, max_active=3, check_interval=50) as srv:
         ids = []
