@@ -46,6 +46,24 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(x: float, ws: int, device: str = "cpu") -> float:
+    """The largest x over all ranks (the slowest rank's time); x itself at
+    one rank.  NCCL needs device="cuda", gloo takes "cpu"."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes_per_rank: float, ws: int, ms_max: float) -> float:
+    """Weak scaling: every rank updates nodes_per_rank nodes in the timed
+    region; the job's rate is all ranks' updates over the slowest rank's time."""
+    return nodes_per_rank * ws / (ms_max * 1e-3) / 1e6
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -268,13 +286,9 @@ def run_ours(args):
         ms, N, launches, tuned = _time_form(clbm, torch, head, args.steps, args.warmup, stream)
         barrier()
     clocks = clk.summary()
-    ms_t = torch.tensor([ms], device="cuda")
-    if ws > 1:
-        import torch.distributed as dist
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, ws, device="cuda")
     nodes = N * len(NS_BENCH) * args.steps
-    value = nodes * ws / (ms_max * 1e-3) / 1e6
+    value = whole_job_mlups(nodes, ws, ms_max)
     per_launch_s = ms * 1e-3 / launches
     bpn = 38 * BYTES_PER_POP[head]
     achieved = bpn * N / per_launch_s / 1e9
