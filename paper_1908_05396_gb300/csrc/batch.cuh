@@ -25,6 +25,7 @@ struct LatDesc {
   unsigned facebits;
   int tiles_x, tiles_y, tile_begin;
   int slot;            // row of this lattice in the batch's reduction array
+  unsigned step_offset;  // F16R: lattice steps minus batch steps (seeds its rounding)
   R lidc[Q];
   CollideConst<R> C;
 };
@@ -76,7 +77,7 @@ __device__ __forceinline__ void batch_node(const LatDesc<R>& L, const S* __restr
 // kernels, the only translation unit that instantiates the batch with REF).
 template <bool FORCE>
 __device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y, int z,
-                               NodeOut<float>& o);
+                               unsigned step, NodeOut<float>& o);
 
 // tile word: x tile (8 bits) | y tile (12 bits) | z chunk (12 bits)
 __host__ __device__ __forceinline__ unsigned tile_word(int tx, int ty, int tz) {
@@ -91,6 +92,9 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
                                             const unsigned* __restrict__ coord,
                                             BatchHeader* hdr, int parity, double* acc) {
   // tiles [0, ntiles0) belong to lattices without force, [ntiles0, ntiles) with
+  // F16R: the batch's step count, advanced at the end of every step by the
+  // last CTA of the forced launch (the second launch of each step)
+  const unsigned bstep = REF ? *reinterpret_cast<volatile const unsigned*>(&hdr->step) : 0u;
   const int t0 = FORCE ? hdr->ntiles0 : 0;
   const int t1 = FORCE ? hdr->ntiles : hdr->ntiles0;
   const int nlat = hdr->nlat;
@@ -130,7 +134,7 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
     if (active) {
       {
         NodeOut<R> o;
-        if constexpr (REF) batch_node_ref<FORCE>(L, parity, x, y, z, o);
+        if constexpr (REF) batch_node_ref<FORCE>(L, parity, x, y, z, bstep + L.step_offset, o);
         else batch_node<S, R, FORCE>(L, src, dst, x, y, z, o);
         if (CHECK) {
           R* up = static_cast<R*>(L.uprev);
@@ -162,6 +166,18 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
         atomicOr(reinterpret_cast<int*>(&a[3]), 1);
     }
   }
+  if constexpr (REF && FORCE) {
+    // every CTA of this step's last launch has read the step count: the last
+    // one to finish advances it
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      __threadfence();
+      if (atomicAdd(&hdr->done, 1) == int(gridDim.x) - 1) {
+        atomicExch(&hdr->done, 0);
+        atomicAdd(&hdr->step, 1u);
+      }
+    }
+  }
 }
 
 // Bytes of __constant__ memory given to the descriptor table of one storage
@@ -172,7 +188,7 @@ constexpr int BATCH_CONST_BYTES = 60 * 1024;
 template <typename R>
 void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur, const void* other,
                  const void* ref_cur, const void* ref_other, void* uprev, int tiles_x,
-                 int tiles_y, int tile_begin, int slot) {
+                 int tiles_y, int tile_begin, int slot, unsigned step_offset) {
   LatDesc<R> L{};
   L.buf[0] = cur;
   L.buf[1] = other;
@@ -190,6 +206,7 @@ void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur,
   L.tiles_y = tiles_y;
   L.tile_begin = tile_begin;
   L.slot = slot;
+  L.step_offset = step_offset;
   for (int q = 0; q < Q; ++q)
     L.lidc[q] = R(6.0 * wt<double>(q) * g.rho0 *
                   (cx(q) * g.U[0] + cy(q) * g.U[1] + cz(q) * g.U[2]));
@@ -241,8 +258,8 @@ void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur,
   int desc_capacity_##SUFFIX() { return int(BATCH_CONST_BYTES / sizeof(LatDesc<R>)); }         \
   void fill_desc_##SUFFIX(void* out, const Geom& g, const PhysParams& P, const void* cur,        \
                           const void* other, const void* ref_cur, const void* ref_other,       \
-                          void* uprev, int tx, int ty, int tb, int slot) {                     \
-    fill_desc_t<R>(out, g, P, cur, other, ref_cur, ref_other, uprev, tx, ty, tb, slot);        \
+                          void* uprev, int tx, int ty, int tb, int slot, unsigned so) {        \
+    fill_desc_t<R>(out, g, P, cur, other, ref_cur, ref_other, uprev, tx, ty, tb, slot, so);    \
   }                                                                                            \
   cudaError_t upload_desc_##SUFFIX(const void* host, int base, int n) {                        \
     return cudaMemcpyToSymbol(c_lat_##SUFFIX, host, size_t(n) * sizeof(LatDesc<R>),            \

@@ -125,20 +125,21 @@ cudaError_t upload_desc(clbm_dtype t, const void* host, int base, int n) {
                           : upload_desc_f16(host, base, n);
 }
 
-void fill_desc(clbm_dtype t, void* out, const clbm_ctx* h, int tx, int ty, int tb, int slot) {
+void fill_desc(clbm_dtype t, void* out, const clbm_ctx* h, int tx, int ty, int tb, int slot,
+               unsigned so) {
   const void* cur = h->buf[h->cur];
   const void* other = h->buf[1 - h->cur];
   // F16R: the reference moments travel with their population buffers
   const void* rcur = h->ref[h->cur];
   const void* rother = h->ref[1 - h->cur];
   if (t == CLBM_F64)
-    fill_desc_f64(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot);
+    fill_desc_f64(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot, so);
   else if (t == CLBM_F32)
-    fill_desc_f32(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot);
+    fill_desc_f32(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot, so);
   else if (t == CLBM_F16R)
-    fill_desc_f16r(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot);
+    fill_desc_f16r(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot, so);
   else
-    fill_desc_f16(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot);
+    fill_desc_f16(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot, so);
 }
 
 cudaError_t launch(clbm_batch_ctx* b, bool check) {
@@ -181,7 +182,10 @@ int upload(clbm_batch_ctx* b) {
       const int tz = h->g.nz;
       if (tx > 255 || ty > 4095 || tz > 4095)
         return bfail(b, CLBM_ERR_UNSUPPORTED, "lattice has too many tiles for the batch table");
-      fill_desc(b->dtype, stage + size_t(nlat) * b->desc_bytes, h, tx, ty, ntiles, s);
+      // the lattice's step count minus the batch's: the kernels add the
+      // batch's device-side count to recover the lattice's own
+      const unsigned so = unsigned(uint64_t(h->steps) - uint64_t(b->steps));
+      fill_desc(b->dtype, stage + size_t(nlat) * b->desc_bytes, h, tx, ty, ntiles, s, so);
       for (int kz = 0; kz < tz; ++kz)
         for (int ky = 0; ky < ty; ++ky)
           for (int kx = 0; kx < tx; ++kx) {
@@ -204,7 +208,7 @@ int upload(clbm_batch_ctx* b) {
     b->owner_cap = cap;
     drop_graph(b);  // the graph holds the old table address
   }
-  BatchHeader hdr{nlat, ntiles, ntiles0, 0};
+  BatchHeader hdr{nlat, ntiles, ntiles0, 0, unsigned(uint64_t(b->steps)), 0};
   if (nlat) BCK(b, upload_desc(b->dtype, stage, b->desc_base, nlat));
   if (ntiles) {
     BCK(b, cudaMemcpy(b->d_owner, b->h_owner.data(), size_t(ntiles) * sizeof(int),

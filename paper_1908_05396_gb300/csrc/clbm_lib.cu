@@ -55,7 +55,7 @@ cudaError_t dispatch_step(clbm_ctx* h, bool check) {
     case CLBM_F32: return launch_step_f32(src, dst, h->g, h->P, cb, check, h->block, h->npt, h->stream);
     case CLBM_F16R:
       return launch_step_f16r(src, dst, h->ref[h->cur], h->ref[1 - h->cur], h->g, h->P, cb, check,
-                              h->block, h->npt, h->stream);
+                              h->block, h->npt, h->steps, h->stream);
     default: return launch_step_f16(src, dst, h->g, h->P, cb, check, h->block, h->npt, h->stream);
   }
 }

@@ -80,6 +80,8 @@ struct BatchHeader {
   int ntiles;   // all tiles
   int ntiles0;  // tiles of lattices without body force (they come first)
   int err;      // set by the kernel if a tile's descriptor fails its checks
+  unsigned step;  // batch steps done (F16R: the kernels derive each lattice's step)
+  int done;       // F16R: CTAs of the forced launch finished in this step
 };
 #define CLBM_DECLARE_BATCH(SUFFIX)                                                              \
   cudaError_t launch_batch_##SUFFIX(int base, const int* owner, const unsigned* coord,         \
@@ -90,17 +92,18 @@ struct BatchHeader {
   cudaError_t upload_desc_##SUFFIX(const void* host, int base, int n);                          \
   void fill_desc_##SUFFIX(void* out, const Geom& g, const PhysParams& P, const void* cur,       \
                           const void* other, const void* ref_cur, const void* ref_other,      \
-                          void* uprev, int tx, int ty, int tb, int slot);
+                          void* uprev, int tx, int ty, int tb, int slot, unsigned step_offset);
 CLBM_DECLARE_BATCH(f64)
 CLBM_DECLARE_BATCH(f32)
 CLBM_DECLARE_BATCH(f16)
 CLBM_DECLARE_BATCH(f16r)
 
 // F16R form (step_f16r.cu): FP16 populations relative to each node's stored
-// first-order equilibrium reference.
+// first-order equilibrium reference, stored with stochastic rounding; `step`
+// is the lattice's count of steps done before this one (it seeds the rounding).
 cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, void* ref_dst,
                              const Geom& g, const PhysParams& P, const CheckBufs& cb, bool check,
-                             dim3 block, int npt, cudaStream_t st);
+                             dim3 block, int npt, int64_t step, cudaStream_t st);
 cudaError_t launch_fields_f16r(const void* src, const void* ref, const Geom& g,
                                const PhysParams& P, double* rho, double* u, double* gd,
                                cudaStream_t st);

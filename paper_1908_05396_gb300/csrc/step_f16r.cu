@@ -6,7 +6,8 @@
 //     s_q = fp16( 1024 * ( f~_q - w_q rho0 - r_q ) ),
 //     r_q = w_q [ drho + 3 (rho0 + drho) (e_q . u) ]        (reference values),
 // which removes the rest value and the first-order (velocity) part of the
-// equilibrium, the largest parts of f~, before FP16 rounding.  A reader
+// equilibrium, the largest parts of f~, before FP16 rounding (stochastic in
+// the step kernels, see enc16_sr).  A reader
 // decodes with the reference of the node that wrote the value: the upwind
 // neighbour for a streamed value, itself for a bounced one.  Both sides use
 // the reference exactly as stored (rounded to FP16), so the encoding is
@@ -48,10 +49,40 @@ __device__ __forceinline__ float ref_term(int q, const Ref4& r, float rho0) {
 __device__ __forceinline__ float dec16(__half v) { return __half2float(v) * float(1.0 / F16_SCALE); }
 __device__ __forceinline__ __half enc16(float v) { return __float2half_rn(v * float(F16_SCALE)); }
 
+// Stochastic rounding of the stores: a value is rounded up in magnitude with
+// probability equal to the fraction of an FP16 ulp it carries, so increments
+// far below one ulp (a weak body force, a slow transient) survive on average
+// instead of being rounded away every step.  FP16 keeps 10 of FP32's 23
+// mantissa bits: a uniform 13-bit integer is added to the FP32 bit pattern and
+// the 13 low bits are cleared, which leaves a value FP16 holds exactly
+// (magnitudes below the FP16 normal range lose their last bits toward zero).
+// The random bits depend only on the node index, the direction and the
+// lattice's own step count, so a lattice gives the same result alone and in
+// a batch: one integer hash of (node, step) (the finaliser of MurmurHash3),
+// then one step per direction of a 32-bit linear congruential generator with
+// the multiplier and increment of PCG (O'Neill, 2014), whose top 13 bits are
+// used.
+__device__ __forceinline__ uint32_t sr_seed(uint32_t node, uint32_t step) {
+  uint32_t h = node ^ (step * 0x9E3779B9u);
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ __half enc16_sr(float v, uint32_t& state) {
+  state = state * 747796405u + 2891336453u;
+  uint32_t b = __float_as_uint(v * float(F16_SCALE));
+  b = (b + (state >> 19)) & 0xFFFFE000u;
+  return __float2half_rz(__uint_as_float(b));
+}
+
 struct RefArgs {
   const uint2* refq[Q];  // refq[q][i]: reference of the upwind neighbour of node i
   const uint2* ref_src;  // references of the source step
   uint2* ref_dst;        // references written by this step
+  unsigned step;         // the lattice's steps done before this one
 };
 
 // Pull of all 19 directions into node (x, y, z) with index i, for a node on
@@ -139,8 +170,9 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
     collide<float, FORCE>(a.C, d, o);
     Ref4 rr;
     r.ref_dst[i] = ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rr);
+    uint32_t rs = sr_seed(uint32_t(i), r.step);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) a.dstq[q][i] = enc16(d[q] - ref_term(q, rr, rho0));
+    for (int q = 0; q < Q; ++q) a.dstq[q][i] = enc16_sr(d[q] - ref_term(q, rr, rho0), rs);
     if (CHECK) {
       float* up = reinterpret_cast<float*>(a.cb.uprev);
       const int64_t nst = int64_t(a.plane) * a.nz;
@@ -286,7 +318,7 @@ void lid_table(const Geom& g, float* out) {
 // and collision as step_ref_kernel.
 template <bool FORCE>
 __device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y, int z,
-                               NodeOut<float>& o) {
+                               unsigned step, NodeOut<float>& o) {
   const __half* src = static_cast<const __half*>(L.buf[parity]);
   __half* dst = static_cast<__half*>(const_cast<void*>(L.buf[parity ^ 1]));
   const uint2* rs = static_cast<const uint2*>(L.ref[parity]);
@@ -325,15 +357,17 @@ __device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y
   collide<float, FORCE>(L.C, d, o);
   Ref4 rr;
   rd[i] = ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rr);
+  uint32_t rst = sr_seed(uint32_t(i), step);
 #pragma unroll
-  for (int q = 0; q < Q; ++q) dst[q * qs + i] = enc16(d[q] - ref_term(q, rr, rho0));
+  for (int q = 0; q < Q; ++q) dst[q * qs + i] = enc16_sr(d[q] - ref_term(q, rr, rho0), rst);
 }
 
 cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, void* ref_dst,
                              const Geom& g, const PhysParams& P, const CheckBufs& cb, bool check,
-                             dim3 block, int npt, cudaStream_t st) {
+                             dim3 block, int npt, int64_t step, cudaStream_t st) {
   StepArgs<__half, float> a;
   RefArgs r;
+  r.step = unsigned(uint64_t(step));
   const __half* s = static_cast<const __half*>(src);
   __half* d = static_cast<__half*>(dst);
   const uint2* rs = static_cast<const uint2*>(ref_src);
