@@ -137,11 +137,15 @@ class Lattice:
             _check(rc, self._h)
         return rc
 
-    def fields(self):
-        """(rho (nz,ny,nx), u (3,nz,ny,nx), gamma_dot (nz,ny,nx)) as FP64 numpy arrays."""
-        rho = np.empty(self.shape)
-        u = np.empty((3,) + self.shape)
-        gd = np.empty(self.shape)
+    def fields(self, out=None):
+        """(rho (nz,ny,nx), u (3,nz,ny,nx), gamma_dot (nz,ny,nx)) as FP64 numpy arrays;
+        `out` may give the three host arrays to fill (e.g. views of pinned memory)."""
+        if out is None:
+            rho, u, gd = np.empty(self.shape), np.empty((3,) + self.shape), np.empty(self.shape)
+        else:
+            rho, u, gd = out
+            for a, shp in ((rho, self.shape), (u, (3,) + self.shape), (gd, self.shape)):
+                assert a.dtype == np.float64 and a.flags.c_contiguous and a.shape == shp
         _check(lib().clbm_fields(self._h, _dp(rho), _dp(u), _dp(gd)), self._h)
         return rho, u, gd
 

@@ -114,8 +114,16 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
     return fail(nullptr, CLBM_ERR_ARG, "unknown dtype");
   if (d->nx < 1 || d->ny < 1 || d->nz < 1)
     return fail(nullptr, CLBM_ERR_ARG, "lattice dimensions must be >= 1");
-  const int64_t N = int64_t(d->nx) * d->ny * d->nz;
-  if (N > (int64_t(1) << 34)) return fail(nullptr, CLBM_ERR_ARG, "lattice too large");
+  // The kernels index one direction's array (padded rows, 128-byte pitch)
+  // with 32-bit integers, neighbours included: keep it well below 2^31.
+  {
+    const int64_t elem = dtype == CLBM_F64 ? 8 : dtype == CLBM_F32 ? 4 : 2;
+    const int64_t pitch = (int64_t(d->nx) + 128 / elem - 1) / (128 / elem) * (128 / elem);
+    const int64_t padded = pitch * d->ny * d->nz;
+    if (padded > (int64_t(1) << 31) - (int64_t(1) << 24))
+      return fail(nullptr, CLBM_ERR_ARG,
+                  "lattice too large: at most 2^31 - 2^24 padded nodes (32-bit indexing)");
+  }
   bool has_lid = false;
   for (int f = 0; f < 6; ++f) {
     if (d->face[f] < CLBM_PERIODIC || d->face[f] > CLBM_LID)

@@ -61,6 +61,8 @@ def _create(clbm, **kw):
     (dict(face=(0, 0, 1, 2, 0, 0), U=(0.4, 0, 0)), "< 0.3"),
     (dict(face=(0, 0, 1, 2, 0, 0), U=(0, 0.05, 0)), "tangential"),
     (dict(face=(0, 0, 5, 1, 0, 0)), "face kind"),
+    (dict(dims=(1400, 1400, 1400), dtype=2), "too large"),   # fits HBM in FP16, not int32
+    (dict(dims=(1290, 1290, 1290), dtype=1), "too large"),
 ])
 def test_create_rejects_bad_arguments(clbm, kw, frag):
     rc, msg = _create(clbm, **kw)

@@ -251,6 +251,25 @@ def test_full_size_cavity_one_step(clbm, oracle, dtype, launch):
         assert np.all(np.abs(f_gpu - f_ref) <= (dev + first) * 2.0 ** -10 + 2e-6)
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_precision_lattice_one_step(clbm, oracle, dtype):
+    # 256^3 cavity, Re 1000, n 0.8 (the lattice of the precision study, the
+    # largest of the workloads): one step from a random perturbed state,
+    # every node compared with the oracle.
+    prob = wl.cavity(256, 1000.0, 0.8)
+    p = _oracle_params(oracle, prob)
+    r = wl.noise((19, 256, 256, 256), seed=4, amp=0.02)
+    with _lattice(clbm, prob, dtype) as lat:
+        rest = lat.get_state()
+        lat.set_state(rest * (1 + r))
+        del rest
+        lat.step(1)
+        f_gpu = lat.get_state()
+    f_ref = oracle.run(p, oracle.rest_state(p) * (1 + r), 1)
+    del r
+    assert np.abs(f_gpu - f_ref).max() <= (1e-14 if dtype == "f64" else 1e-6)
+
+
 _PERX = wl.Problem("perx", 70, 37, 11, (wl.PERIODIC, wl.PERIODIC, wl.WALL, wl.LID, wl.WALL, wl.WALL),
                    K=0.02, n=1.3, U_lid=(0.05, 0.0, 0.01))
 
