@@ -90,7 +90,7 @@ __host__ __device__ __forceinline__ unsigned tile_word(int tx, int ty, int tz) {
 template <typename S, typename R, bool CHECK, bool FORCE, bool REF, typename Get>
 __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ owner,
                                             const unsigned* __restrict__ coord,
-                                            BatchHeader* hdr, int parity, double* acc) {
+                                            BatchHeader* hdr, int parity, double* acc, int zc) {
   // tiles [0, ntiles0) belong to lattices without force, [ntiles0, ntiles) with
   // F16R: the batch's step count, advanced at the end of every step by the
   // last CTA of the forced launch (the second launch of each step)
@@ -116,7 +116,7 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
     const LatDesc<R>& L = get(ok ? li : 0);
     if (ok)
       ok = L.buf[0] != nullptr && L.buf[1] != nullptr && tx < L.tiles_x && ty < L.tiles_y &&
-           tz < L.nz && L.pitch >= L.nx && L.plane == L.pitch * L.ny &&
+           zc >= 1 && tz * zc < L.nz && L.pitch >= L.nx && L.plane == L.pitch * L.ny &&
            L.qstride >= int64_t(L.plane) * L.nz && 19 * L.qstride < (int64_t(1) << 31) &&
            (L.C.has_force != 0) == FORCE && (!REF || (L.ref[0] != nullptr && L.ref[1] != nullptr));
     if (!ok) {  // block-uniform: skip the tile, report it
@@ -125,14 +125,17 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
     }
     const int x = tx * blockDim.x + threadIdx.x;
     const int y = ty * blockDim.y + threadIdx.y;
-    const int z = tz;
     const S* src = static_cast<const S*>(L.buf[parity]);
     S* dst = static_cast<S*>(const_cast<void*>(L.buf[parity ^ 1]));
     const bool active = x < L.nx && y < L.ny;
     double du2 = 0.0, uu = 0.0, dr = 0.0;
     int bad = 0;
-    if (active) {
-      {
+    // the tile's zc planes: the per-tile work (table entries, descriptor,
+    // checks, the check-step reductions) is shared by zc nodes per thread
+    const int z1 = min(tz * zc + zc, L.nz);
+#pragma unroll 1
+    for (int z = tz * zc; z < z1; ++z) {
+      if (active) {
         NodeOut<R> o;
         if constexpr (REF) batch_node_ref<FORCE>(L, parity, x, y, z, bstep + L.step_offset, o);
         else batch_node<S, R, FORCE>(L, src, dst, x, y, z, o);
@@ -223,33 +226,33 @@ void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur,
   __global__ void __launch_bounds__(256, CAP ? 4 : 1)                                          \
       batch_kernel_##SUFFIX(int base, const int* __restrict__ owner,                           \
                             const unsigned* __restrict__ coord, BatchHeader* hdr, int parity,  \
-                            double* acc) {                                                     \
+                            double* acc, int zc) {                                             \
     batch_tiles<S, R, CHECK, FORCE, REF>(                                                      \
         [base](int li) -> const LatDesc<R>& { return c_lat_##SUFFIX[base + li]; }, owner,      \
-        coord, hdr, parity, acc);                                                              \
+        coord, hdr, parity, acc, zc);                                                          \
   }                                                                                            \
   cudaError_t launch_batch_##SUFFIX(int base, const int* owner, const unsigned* coord,         \
                                     const void* hdr, int parity, bool check, double* acc,      \
-                                    dim3 block, int grid, cudaStream_t st) {                   \
+                                    int zc, dim3 block, int grid, cudaStream_t st) {           \
     BatchHeader* H = static_cast<BatchHeader*>(const_cast<void*>(hdr));                        \
     const bool cap = grid < 0;                                                                 \
     if (cap) grid = -grid;                                                                     \
     /* tiles without force, then tiles with force (an empty range exits at once) */           \
     if (check) {                                                                               \
       if (cap) {                                                                               \
-        batch_kernel_##SUFFIX<true, true, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
-        batch_kernel_##SUFFIX<true, true, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
+        batch_kernel_##SUFFIX<true, true, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<true, true, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
       } else {                                                                                 \
-        batch_kernel_##SUFFIX<true, false, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
-        batch_kernel_##SUFFIX<true, false, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
+        batch_kernel_##SUFFIX<true, false, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<true, false, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
       }                                                                                        \
     } else {                                                                                   \
       if (cap) {                                                                               \
-        batch_kernel_##SUFFIX<false, true, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
-        batch_kernel_##SUFFIX<false, true, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
+        batch_kernel_##SUFFIX<false, true, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<false, true, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
       } else {                                                                                 \
-        batch_kernel_##SUFFIX<false, false, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
-        batch_kernel_##SUFFIX<false, false, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc); \
+        batch_kernel_##SUFFIX<false, false, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<false, false, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
       }                                                                                        \
     }                                                                                          \
     return cudaGetLastError();                                                                 \

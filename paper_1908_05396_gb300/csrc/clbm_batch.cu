@@ -147,16 +147,16 @@ cudaError_t launch(clbm_batch_ctx* b, bool check) {
   switch (b->dtype) {
     case CLBM_F64:
       return launch_batch_f64(b->desc_base, b->d_owner, b->d_coord, b->d_hdr, b->parity, check,
-                              b->d_acc, b->block, grid, b->stream);
+                              b->d_acc, b->zc, b->block, grid, b->stream);
     case CLBM_F32:
       return launch_batch_f32(b->desc_base, b->d_owner, b->d_coord, b->d_hdr, b->parity, check,
-                              b->d_acc, b->block, grid, b->stream);
+                              b->d_acc, b->zc, b->block, grid, b->stream);
     case CLBM_F16R:
       return launch_batch_f16r(b->desc_base, b->d_owner, b->d_coord, b->d_hdr, b->parity, check,
-                               b->d_acc, b->block, grid, b->stream);
+                               b->d_acc, b->zc, b->block, grid, b->stream);
     default:
       return launch_batch_f16(b->desc_base, b->d_owner, b->d_coord, b->d_hdr, b->parity, check,
-                              b->d_acc, b->block, grid, b->stream);
+                              b->d_acc, b->zc, b->block, grid, b->stream);
   }
 }
 
@@ -179,7 +179,7 @@ int upload(clbm_batch_ctx* b) {
       if (!h || (h->P.has_force != 0) != (pass == 1)) continue;
       const int tx = (h->g.nx + int(b->block.x) - 1) / int(b->block.x);
       const int ty = (h->g.ny + int(b->block.y) - 1) / int(b->block.y);
-      const int tz = h->g.nz;
+      const int tz = (h->g.nz + b->zc - 1) / b->zc;   // chunks of zc planes
       if (tx > 255 || ty > 4095 || tz > 4095)
         return bfail(b, CLBM_ERR_UNSUPPORTED, "lattice has too many tiles for the batch table");
       // the lattice's step count minus the batch's: the kernels add the
@@ -474,7 +474,7 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
   const dim3 block0 = b->block;
   const int zc0 = b->zc, bps0 = b->blocks_per_sm;
   const int shapes[][2] = {{32, 2}, {32, 4}, {32, 8}, {64, 2}, {64, 4}, {128, 1}, {128, 2}};
-  const int zcs[] = {1};
+  const int zcs[] = {1, 2, 4};
   const int bpss[] = {4, 6, 8};
   const bool cap0 = b->cap;
   double best = 1e300;

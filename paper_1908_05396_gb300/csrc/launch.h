@@ -86,7 +86,7 @@ struct BatchHeader {
 #define CLBM_DECLARE_BATCH(SUFFIX)                                                              \
   cudaError_t launch_batch_##SUFFIX(int base, const int* owner, const unsigned* coord,         \
                                     const void* hdr, int parity, bool check, double* acc,       \
-                                    dim3 block, int grid, cudaStream_t st);                     \
+                                    int zc, dim3 block, int grid, cudaStream_t st);             \
   size_t desc_size_##SUFFIX();                                                                  \
   int desc_capacity_##SUFFIX();                                                                 \
   cudaError_t upload_desc_##SUFFIX(const void* host, int base, int n);                          \
