@@ -224,7 +224,7 @@ def run_reference(args):
     return 0
 
 
-def _time_form(clbm, torch, dtype, steps, warmup, stream):
+def _time_form(clbm, torch, dtype, steps, warmup, stream, in_place=False):
     """MLUPS of one storage form over the three cavities, each lattice stepping
     on its own stream so that one lattice's launch gaps and tail waves are
     filled by the others' work; the timed region is fenced by events on
@@ -232,7 +232,7 @@ def _time_form(clbm, torch, dtype, steps, warmup, stream):
     from paper_1908_05396_gb300 import workloads as wl
     streams = [torch.cuda.Stream() for _ in NS_BENCH]
     lats = [clbm.Lattice(**wl.cavity(L_BENCH, RE_BENCH, n).kwargs(), dtype=dtype,
-                         stream=s.cuda_stream) for n, s in zip(NS_BENCH, streams)]
+                         stream=s.cuda_stream, in_place=in_place) for n, s in zip(NS_BENCH, streams)]
     tuned = [lt.autotune(10) for lt in lats]     # launch shape per lattice (cached)
     N = lats[0].N
     for _ in range(warmup):
@@ -304,17 +304,21 @@ def run_ours(args):
     # ---- the other forms ------------------------------------------------------
     forms = {}
     form_steps = {"f64": max(3, args.steps // 40), "f16s": args.steps}
-    for dt in ("f64", "f16s"):
-        if args.forms and dt not in args.forms:
+    form_steps["f32_inplace"] = args.steps
+    for name in ("f64", "f16s", "f32_inplace"):
+        if args.forms and name not in args.forms:
             continue
+        dt, ip = (name[:-len("_inplace")], True) if name.endswith("_inplace") else (name, False)
         barrier()
-        ms_f, N_f, launches_f, tuned_f = _time_form(clbm, torch, dt, form_steps[dt], args.warmup,
-                                                    stream)
-        mlups = N_f * len(NS_BENCH) * form_steps[dt] / (ms_f * 1e-3) / 1e6
+        ms_f, N_f, launches_f, tuned_f = _time_form(clbm, torch, dt, form_steps[name], args.warmup,
+                                                    stream, in_place=ip)
+        mlups = N_f * len(NS_BENCH) * form_steps[name] / (ms_f * 1e-3) / 1e6
         gbs = 38 * BYTES_PER_POP[dt] * N_f * launches_f / (ms_f * 1e-3) / 1e9
-        forms[dt] = {"MLUPS": mlups, "GB/s": gbs, "frac_of_hbm": gbs / peak,
-                     "steps": form_steps[dt], "bytes_per_update": 38 * BYTES_PER_POP[dt],
-                     "launch": [(t["block"], t["npt"]) for t in tuned_f]}
+        forms[name] = {"MLUPS": mlups, "GB/s": gbs, "frac_of_hbm": gbs / peak,
+                       "steps": form_steps[name], "bytes_per_update": 38 * BYTES_PER_POP[dt],
+                       "launch": [(t["block"], t["npt"]) for t in tuned_f]}
+        if ip:
+            forms[name]["what"] = "one population buffer streamed in place (half the memory)"
     forms[head] = {"MLUPS": value / ws, "GB/s": achieved, "frac_of_hbm": achieved / peak,
                    "steps": args.steps, "bytes_per_update": bpn,
                    "launch": [(t["block"], t["npt"]) for t in tuned]}

@@ -85,6 +85,10 @@ typedef struct {
   double nu_max;       /* 0 -> 10 */
   int check_interval;  /* steps between residual checks; 0 -> 100 */
   void* stream;        /* cudaStream_t to queue on; NULL -> library-owned */
+  int in_place;        /* 1: one population buffer, streamed in place (not in
+                        * the paper): half the memory, the same results and
+                        * bytes per update; FP64, FP32 and F16S only, not in
+                        * batches (the server's lattices ignore it) */
 } clbm_domain;
 
 typedef struct clbm_ctx* clbm_handle;

@@ -33,7 +33,8 @@ class Domain(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("face", ctypes.c_int * 6), ("rho0", ctypes.c_double),
                 ("nu_min", ctypes.c_double), ("nu_max", ctypes.c_double),
-                ("check_interval", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("check_interval", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("in_place", ctypes.c_int)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -108,9 +109,10 @@ class Lattice:
 
     def __init__(self, nx, ny, nz, face=(PERIODIC,) * 6, K=0.1, n=1.0, U_lid=None,
                  body_force=None, dtype="f64", rho0=1.0, nu_min=0.0, nu_max=0.0,
-                 check_interval=100, stream=None):
+                 check_interval=100, stream=None, in_place=False):
         L = lib()
         d = Domain()
+        d.in_place = 1 if in_place else 0
         d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
         for i, f in enumerate(face):
             d.face[i] = int(f)

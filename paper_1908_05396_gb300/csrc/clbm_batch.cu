@@ -349,6 +349,8 @@ int clbm_batch_create(clbm_dtype dtype, int capacity, int check_interval, void* 
 int clbm_batch_add(clbm_batch b, clbm_handle h, int* slot) {
   if (!valid(b) || !h || !h->buf[0]) return bfail(b, CLBM_ERR_ARG, "invalid batch or handle");
   if (h->dtype != b->dtype) return bfail(b, CLBM_ERR_ARG, "lattice dtype differs from the batch's");
+  if (h->in_place)
+    return bfail(b, CLBM_ERR_UNSUPPORTED, "in-place lattices are not batched (two-buffer tiles)");
   if (h->device != b->device) return bfail(b, CLBM_ERR_ARG, "lattice lives on another device");
   if (h->batch) return bfail(b, CLBM_ERR_ARG, "lattice is already in a batch");
   if (int64_t(NQ) * h->g.qstride >= (int64_t(1) << 31))

@@ -48,6 +48,14 @@ int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 cudaError_t dispatch_step(clbm_ctx* h, bool check) {
   CheckBufs cb{h->uprev, h->acc, h->flag};
+  if (h->in_place) {
+    const int npt = h->npt & 4 ? 5 : 1;
+    switch (h->dtype) {
+      case CLBM_F64: return launch_step_aa_f64(h->buf[0], h->g, h->P, cb, check, h->block, npt, h->layout, h->stream);
+      case CLBM_F32: return launch_step_aa_f32(h->buf[0], h->g, h->P, cb, check, h->block, npt, h->layout, h->stream);
+      default: return launch_step_aa_f16(h->buf[0], h->g, h->P, cb, check, h->block, npt, h->layout, h->stream);
+    }
+  }
   const void* src = h->buf[h->cur];
   void* dst = h->buf[1 - h->cur];
   switch (h->dtype) {
@@ -58,6 +66,13 @@ cudaError_t dispatch_step(clbm_ctx* h, bool check) {
                               h->block, h->npt, h->steps, h->stream);
     default: return launch_step_f16(src, dst, h->g, h->P, cb, check, h->block, h->npt, h->stream);
   }
+}
+
+// After a step: the other buffer holds the state, or (in place) the buffer
+// holds the other layout.
+void advance_state(clbm_ctx* h) {
+  if (h->in_place) h->layout ^= 1;
+  else h->cur = 1 - h->cur;
 }
 
 int set_device(clbm_ctx* h) {
@@ -112,6 +127,8 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
   *out = nullptr;
   if (dtype != CLBM_F64 && dtype != CLBM_F32 && dtype != CLBM_F16S && dtype != CLBM_F16R)
     return fail(nullptr, CLBM_ERR_ARG, "unknown dtype");
+  if (d->in_place && dtype == CLBM_F16R)
+    return fail(nullptr, CLBM_ERR_UNSUPPORTED, "in-place streaming takes FP64, FP32 or F16S storage");
   if (d->nx < 1 || d->ny < 1 || d->nz < 1)
     return fail(nullptr, CLBM_ERR_ARG, "lattice dimensions must be >= 1");
   // The kernels index one direction's array (padded rows, 128-byte pitch)
@@ -199,7 +216,8 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
     h->own_stream = true;
   }
   const size_t pop_bytes = size_t(NQ) * size_t(g.qstride) * h->elem;
-  for (int b = 0; b < 2; ++b) {
+  h->in_place = d->in_place != 0;
+  for (int b = 0; b < (h->in_place ? 1 : 2); ++b) {
     e = cudaMalloc(&h->buf[b], pop_bytes);
     if (e != cudaSuccess) return cleanup(CLBM_ERR_OOM, "population buffer allocation failed");
   }
@@ -223,7 +241,7 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
   e = cudaEventCreateWithFlags(&h->check_done, cudaEventDisableTiming);
   if (e != cudaSuccess) return cleanup(CLBM_ERR_CUDA, cudaGetErrorString(e));
   // Rest state: stored deviation f - w rho0 = 0 (all-zero bits in every form).
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < (h->in_place ? 1 : 2); ++b) {
     e = cudaMemsetAsync(h->buf[b], 0, pop_bytes, h->stream);
     if (e != cudaSuccess) return cleanup(CLBM_ERR_CUDA, cudaGetErrorString(e));
   }
@@ -245,7 +263,7 @@ int clbm_step(clbm_handle h, int64_t nsteps) {
     const bool check = ((h->steps + 1) % every) == 0;
     if (check) CK(h, cudaMemsetAsync(h->acc, 0, 3 * sizeof(double), h->stream));
     CK(h, dispatch_step(h, check));
-    h->cur = 1 - h->cur;
+    advance_state(h);
     h->steps += 1;
     if (check) {
       h->checks += 1;
@@ -270,6 +288,15 @@ int clbm_step(clbm_handle h, int64_t nsteps) {
 static int fields_impl(clbm_handle h, double* rho, double* u, double* gd) {
   const void* src = h->buf[h->cur];
   cudaError_t e;
+  if (h->in_place) {
+    switch (h->dtype) {
+      case CLBM_F64: e = launch_fields_aa_f64(src, h->g, h->P, h->layout, rho, u, gd, h->stream); break;
+      case CLBM_F32: e = launch_fields_aa_f32(src, h->g, h->P, h->layout, rho, u, gd, h->stream); break;
+      default: e = launch_fields_aa_f16(src, h->g, h->P, h->layout, rho, u, gd, h->stream); break;
+    }
+    CK(h, e);
+    return CLBM_OK;
+  }
   switch (h->dtype) {
     case CLBM_F64: e = launch_fields_f64(src, h->g, h->P, rho, u, gd, h->stream); break;
     case CLBM_F32: e = launch_fields_f32(src, h->g, h->P, rho, u, gd, h->stream); break;
@@ -355,7 +382,15 @@ static int state_io(clbm_handle h, double* out, const double* in) {
   const double isc = h->P.inv_scale;
   if (in) {
     e = cudaMemcpyAsync(dev, in, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && h->in_place) {
+      // the state goes into the swapped layout
+      switch (h->dtype) {
+        case CLBM_F64: e = launch_import_aa_f64(dev, h->g, h->g.rho0, isc, h->buf[0], h->stream); break;
+        case CLBM_F32: e = launch_import_aa_f32(dev, h->g, h->g.rho0, isc, h->buf[0], h->stream); break;
+        default: e = launch_import_aa_f16(dev, h->g, h->g.rho0, isc, h->buf[0], h->stream); break;
+      }
+      h->layout = 0;
+    } else if (e == cudaSuccess) {
       switch (h->dtype) {
         case CLBM_F64: e = launch_import_f64(dev, h->g, h->g.rho0, isc, h->buf[h->cur], h->stream); break;
         case CLBM_F32: e = launch_import_f32(dev, h->g, h->g.rho0, isc, h->buf[h->cur], h->stream); break;
@@ -365,6 +400,14 @@ static int state_io(clbm_handle h, double* out, const double* in) {
         default: e = launch_import_f16(dev, h->g, h->g.rho0, isc, h->buf[h->cur], h->stream); break;
       }
     }
+  } else if (h->in_place) {
+    switch (h->dtype) {
+      case CLBM_F64: e = launch_export_aa_f64(h->buf[0], h->g, h->g.rho0, isc, h->layout, dev, h->stream); break;
+      case CLBM_F32: e = launch_export_aa_f32(h->buf[0], h->g, h->g.rho0, isc, h->layout, dev, h->stream); break;
+      default: e = launch_export_aa_f16(h->buf[0], h->g, h->g.rho0, isc, h->layout, dev, h->stream); break;
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out, dev, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   } else {
     switch (h->dtype) {
       case CLBM_F64: e = launch_export_f64(h->buf[h->cur], h->g, h->g.rho0, isc, dev, h->stream); break;
@@ -413,8 +456,8 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
   if (bad(h)) return fail(h, CLBM_ERR_ARG, "invalid handle");
   if (int r = set_device(h)) return r;
   if (steps <= 0) steps = 10;
-  const auto key = std::make_tuple(int(h->dtype), h->g.nx, h->g.ny, h->g.nz, h->P.has_force,
-                                   h->P.newtonian);
+  const auto key = std::make_tuple(int(h->dtype) + (h->in_place ? 16 : 0), h->g.nx, h->g.ny,
+                                   h->g.nz, h->P.has_force, h->P.newtonian);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
@@ -435,14 +478,14 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
   const int shapes[][2] = {{32, 1}, {32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2}, {64, 4},
                            {128, 1}, {128, 2}, {256, 1}};
   for (int capped = 0; capped <= 1; ++capped)
-    for (int np = 1; np <= ((h->dtype == CLBM_F64 || h->dtype == CLBM_F16R) ? 1 : 2); ++np)
+    for (int np = 1; np <= ((h->dtype == CLBM_F64 || h->dtype == CLBM_F16R || h->in_place) ? 1 : 2); ++np)
       for (auto& sh : shapes) {
         if (sh[0] * sh[1] > (np == 2 ? 128 : 256)) continue;
         if (sh[0] > 32 && sh[0] > h->g.pitch) continue;
         cands.push_back({sh[0], sh[1], np + 4 * capped});
       }
   // FP32 and FP16 storage: the TMA-staged kernel in each of its shapes
-  if (h->dtype == CLBM_F32 || h->dtype == CLBM_F16S)
+  if ((h->dtype == CLBM_F32 || h->dtype == CLBM_F16S) && !h->in_place)
     for (int v = 0; v < TMA_NVAR; ++v) cands.push_back({tma_bx(v), tma_by(v), TMA_NPT + 32 * v});
   // Save the state: tuning runs real steps.
   const size_t pop_bytes = size_t(NQ) * size_t(h->g.qstride) * h->elem;
@@ -453,7 +496,7 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
   if (ref_bytes)
     CK(h, cudaMemcpyAsync(static_cast<char*>(saved) + pop_bytes, h->ref[h->cur], ref_bytes,
                           cudaMemcpyDeviceToDevice, h->stream));
-  const int cur0 = h->cur;
+  const int cur0 = h->cur, layout0 = h->layout;
   cudaEvent_t e0, e1;
   CK(h, cudaEventCreate(&e0));
   CK(h, cudaEventCreate(&e1));
@@ -467,12 +510,12 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
     h->npt = c.npt;
     for (int s = 0; s < 2 && err == cudaSuccess; ++s) {
       err = dispatch_step(h, false);
-      h->cur = 1 - h->cur;
+      advance_state(h);
     }
     if (err == cudaSuccess) err = cudaEventRecord(e0, h->stream);
     for (int s = 0; s < steps && err == cudaSuccess; ++s) {
       err = dispatch_step(h, false);
-      h->cur = 1 - h->cur;
+      advance_state(h);
     }
     if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);
@@ -487,8 +530,9 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  // Restore the state into the buffer that held it.
+  // Restore the state into the buffer that held it (and its layout).
   h->cur = cur0;
+  h->layout = layout0;
   cudaError_t e2 = cudaMemcpyAsync(h->buf[h->cur], saved, pop_bytes, cudaMemcpyDeviceToDevice,
                                    h->stream);
   if (e2 == cudaSuccess && ref_bytes)
@@ -517,6 +561,8 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
 
 int clbm_set_launch(clbm_handle h, int block_x, int block_y, int npt) {
   if (bad(h)) return fail(h, CLBM_ERR_ARG, "invalid handle");
+  if (h->in_place && ((npt & TMA_NPT) || (npt & 3) == 2))
+    return fail(h, CLBM_ERR_UNSUPPORTED, "in-place lattices take one node per thread (npt 1 or 5)");
   if (npt & TMA_NPT) {
     const int v = npt >> 5;
     if ((npt & 31) != TMA_NPT || v >= TMA_NVAR)

@@ -167,6 +167,7 @@ void worker_loop(clbm_server_ctx* s) {
       clbm_domain dom = p.req.dom;
       dom.check_interval = s->check_interval;
       dom.stream = nullptr;
+      dom.in_place = 0;   // the batched step works on two buffers
       int rc = clbm_create(&dom, p.req.K, p.req.n, p.req.U_lid, p.req.body_force, s->dtype, &a.h);
       if (rc == CLBM_OK) rc = clbm_batch_add(s->batch, a.h, &a.slot);
       a.t_admit = now(s);

@@ -500,6 +500,7 @@ __global__ void import_kernel(const double* __restrict__ in, Geom g, double rho0
 }  // namespace clbm
 
 #include "tma_step.cuh"
+#include "inplace.cuh"
 
 namespace clbm {
 

@@ -119,4 +119,22 @@ CLBM_DECLARE_LAUNCHERS(f64)
 CLBM_DECLARE_LAUNCHERS(f32)
 CLBM_DECLARE_LAUNCHERS(f16)
 
+// In-place (one buffer) step, fields and state transfer (inplace.cuh);
+// `layout` is the layout the buffer holds (0 swapped, 1 streamed).
+#define CLBM_DECLARE_AA(SUFFIX)                                                                 \
+  cudaError_t launch_step_aa_##SUFFIX(void* buf, const Geom& g, const PhysParams& P,            \
+                                      const CheckBufs& cb, bool check, dim3 block, int npt,     \
+                                      int layout, cudaStream_t st);                             \
+  cudaError_t launch_fields_aa_##SUFFIX(const void* buf, const Geom& g, const PhysParams& P,    \
+                                        int layout, double* rho, double* u, double* gd,         \
+                                        cudaStream_t st);                                       \
+  cudaError_t launch_export_aa_##SUFFIX(const void* buf, const Geom& g, double rho0,            \
+                                        double inv_scale, int layout, double* out,              \
+                                        cudaStream_t st);                                       \
+  cudaError_t launch_import_aa_##SUFFIX(const double* in, const Geom& g, double rho0,           \
+                                        double inv_scale, void* buf, cudaStream_t st);
+CLBM_DECLARE_AA(f64)
+CLBM_DECLARE_AA(f32)
+CLBM_DECLARE_AA(f16)
+
 }  // namespace clbm

@@ -3,4 +3,5 @@
 #include "kernels.cuh"
 
 CLBM_DEFINE_LAUNCHERS(f16, __half, float)
+CLBM_DEFINE_AA(f16, __half, float)
 CLBM_DEFINE_BATCH(f16, __half, float, false)

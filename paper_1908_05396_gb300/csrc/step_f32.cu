@@ -3,4 +3,5 @@
 #include "kernels.cuh"
 
 CLBM_DEFINE_LAUNCHERS(f32, float, float)
+CLBM_DEFINE_AA(f32, float, float)
 CLBM_DEFINE_BATCH(f32, float, float, false)

@@ -3,4 +3,5 @@
 #include "kernels.cuh"
 
 CLBM_DEFINE_LAUNCHERS(f64, double, double)
+CLBM_DEFINE_AA(f64, double, double)
 CLBM_DEFINE_BATCH(f64, double, double, false)

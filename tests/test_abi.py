@@ -41,6 +41,7 @@ def _create(clbm, **kw):
     d.nx, d.ny, d.nz = kw.get("dims", (4, 4, 4))
     for i, f in enumerate(kw.get("face", (0,) * 6)):
         d.face[i] = f
+    d.in_place = kw.get("in_place", 0)
     h = ctypes.c_void_p()
     U = kw.get("U")
     Uc = (ctypes.c_double * 3)(*U) if U is not None else None
@@ -68,6 +69,11 @@ def test_create_rejects_bad_arguments(clbm, kw, frag):
     rc, msg = _create(clbm, **kw)
     assert rc == clbm.ERR_ARG
     assert frag in msg
+
+
+def test_in_place_rejects_the_f16r_form(clbm):
+    rc, msg = _create(clbm, dtype=3, in_place=1)
+    assert rc == clbm.ERR_UNSUPPORTED and "in-place" in msg
 
 
 def test_null_handle_calls_fail_cleanly(clbm):

@@ -1,0 +1,112 @@
+"""In-place streaming (one population buffer): every step must compute what
+the two-buffer step computes, for odd and even step counts (the buffer holds
+one of two layouts between steps), on lattices with walls, the lid, periodic
+faces and a body force; state transfer, fields, residual and mass must agree;
+and the lattice must hold one population buffer instead of two."""
+import numpy as np
+import pytest
+
+from paper_1908_05396_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+
+_MIXED = wl.Problem("mixed", 33, 17, 9, (wl.WALL, wl.WALL, wl.WALL, wl.LID, wl.PERIODIC, wl.PERIODIC),
+                    K=0.01, n=0.7, U_lid=(0.04, 0.0, 0.02), body_force=(1e-5, 0.0, -2e-6))
+_PERX = wl.Problem("perx", 70, 37, 11, (wl.PERIODIC, wl.PERIODIC, wl.WALL, wl.LID, wl.WALL, wl.WALL),
+                   K=0.02, n=1.3, U_lid=(0.05, 0.0, 0.01))
+_BOX = wl.Problem("box", 17, 9, 11, (wl.PERIODIC,) * 6, K=0.02, n=1.3, body_force=(1e-5, -2e-6, 3e-6))
+
+
+@pytest.fixture(scope="module")
+def clbm():
+    from paper_1908_05396_gb300 import build
+    build.build()
+    from paper_1908_05396_gb300 import clbm as c
+    c.lib()
+    return c
+
+
+def _same(f, f_ref, dtype):
+    if dtype == "f64":
+        assert np.abs(f - f_ref).max() <= 1e-13, np.abs(f - f_ref).max()
+    elif dtype == "f32":
+        assert np.abs(f - f_ref).max() <= 1e-6
+    else:
+        dev = np.abs(f_ref - W[:, None, None, None])
+        assert np.all(np.abs(f - f_ref) <= dev * 2.0 ** -10 + 1e-7)
+
+
+@pytest.mark.parametrize("prob", [_MIXED, _PERX, _BOX], ids=["mixed", "perx", "box"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s"])
+def test_in_place_matches_two_buffers(clbm, prob, dtype):
+    r = wl.noise((19, prob.nz, prob.ny, prob.nx), seed=7, amp=0.05)
+    with clbm.Lattice(**prob.kwargs(), dtype=dtype, check_interval=50) as a, \
+            clbm.Lattice(**prob.kwargs(), dtype=dtype, check_interval=50, in_place=True) as b:
+        f0 = a.get_state() * (1 + r)
+        a.set_state(f0)
+        b.set_state(f0)
+        _same(b.get_state(), a.get_state(), dtype)
+        done = 0
+        for n in (1, 1, 35, 63, 100):         # odd and even totals: both layouts
+            a.step(n)
+            b.step(n)
+            done += n
+            _same(b.get_state(), a.get_state(), dtype)
+            ra, ua, ga = a.fields()
+            rb, ub, gb = b.fields()
+            tol = 1e-13 if dtype == "f64" else (1e-6 if dtype == "f32" else 1e-3)
+            assert np.abs(ub - ua).max() <= tol * max(np.abs(ua).max(), 1e-3)
+            assert np.abs(rb - ra).max() <= tol
+        assert done == 200
+        Ra, rca = a.residual()
+        Rb, rcb = b.residual()
+        assert rca == rcb == 0
+        assert abs(Ra - Rb) <= (1e-10 if dtype == "f64" else 1e-3) * Ra
+        assert abs(a.mass() - b.mass()) <= 1e-9 * a.mass()
+
+
+def test_in_place_holds_one_buffer(clbm):
+    import torch
+    prob = wl.cavity(128, 100.0, 0.5)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    with clbm.Lattice(**prob.kwargs(), dtype="f32", in_place=True) as b:
+        b.sync()
+        used_in_place = free0 - torch.cuda.mem_get_info()[0]
+    free0 = torch.cuda.mem_get_info()[0]
+    with clbm.Lattice(**prob.kwargs(), dtype="f32") as a:
+        a.sync()
+        used_two = free0 - torch.cuda.mem_get_info()[0]
+    pop = 19 * 128 * 128 * 128 * 4                  # one FP32 population buffer
+    assert abs((used_two - used_in_place) - pop) <= 0.05 * pop, (used_two, used_in_place)
+
+
+def test_in_place_autotune_restores_state_and_layout(clbm):
+    prob = wl.cavity(40, 200.0, 0.6, dims=(40, 36, 20))
+    with clbm.Lattice(**prob.kwargs(), dtype="f32", in_place=True) as b, \
+            clbm.Lattice(**prob.kwargs(), dtype="f32") as a:
+        a.step(51)
+        b.step(51)                                     # odd: streamed layout
+        f0 = b.get_state()
+        info = b.autotune(5)
+        assert np.array_equal(b.get_state(), f0) and b.steps_done() == 51
+        assert info["npt"] in (1, 5)
+        a.step(149)
+        b.step(149)
+        _same(b.get_state(), a.get_state(), "f32")
+
+
+def test_in_place_limits(clbm):
+    prob = wl.cavity(16, 100.0, 1.0)
+    with pytest.raises(clbm.CLBMError):
+        clbm.Lattice(**prob.kwargs(), dtype="f16r", in_place=True)
+    with clbm.Lattice(**prob.kwargs(), dtype="f32", in_place=True) as b:
+        with pytest.raises(clbm.CLBMError):
+            b.set_launch(32, 4, 2)                     # two nodes per thread: two buffers only
+        with pytest.raises(clbm.CLBMError):
+            b.set_launch(64, 4, 16)                    # the TMA-staged kernel: two buffers only
+        with clbm.Batch("f32", capacity=2) as batch:
+            with pytest.raises(clbm.CLBMError):
+                batch.add(b)
