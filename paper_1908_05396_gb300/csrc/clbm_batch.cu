@@ -51,7 +51,7 @@ struct clbm_batch_ctx {
   int64_t steps = 0;
   bool dirty = true;
   dim3 block{32, 4, 1};
-  int zc = 4;
+  int zc = 1;                         // planes per tile (autotuned)
   int blocks_per_sm = 4;
   bool cap = false;                   // register-capped kernel variant
   int sms = 1;
