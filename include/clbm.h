@@ -179,6 +179,15 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
  * clbm_step / clbm_residual return CLBM_ERR_CUDA. */
 int clbm_set_launch(clbm_handle h, int block_x, int block_y, int npt);
 
+/* Set the relaxation rates omega_9 .. omega_18 of h: the bulk rate (omega_9)
+ * and the third- (omega_10..15) and fourth-order (omega_16..18) rates of the
+ * cascaded collision (Sec. 3.1 sets all to 1; Sec. 5 notes that tuning them
+ * can improve stability).  omega[k] is omega_(9+k); each must lie in (0, 2).
+ * omega_9 also scales the isotropic part of the strain rate that sets
+ * omega_nu.  Takes effect from the next step.  Not for a lattice in a batch
+ * (CLBM_ERR_ARG: detach it first).  Errors: CLBM_ERR_ARG. */
+int clbm_set_rates(clbm_handle h, const double omega[10]);
+
 /* ---- Batched stepping of many lattices --------------------------------
  * Not in the paper: a batch steps up to `capacity` lattices of one storage
  * form (any of the four, F16R with its reference moments) together, one launch of a persistent kernel per time step for all of

@@ -76,7 +76,8 @@ def lib():
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         _D]
             L.clbm_set_launch.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int]
-            for name in ("clbm_autotune", "clbm_set_launch",
+            L.clbm_set_rates.argtypes = [_H, _D]
+            for name in ("clbm_autotune", "clbm_set_launch", "clbm_set_rates",
                          "clbm_create", "clbm_step", "clbm_fields", "clbm_fields_device",
                          "clbm_residual", "clbm_mass", "clbm_get_state", "clbm_set_state",
                          "clbm_steps_done", "clbm_sync", "clbm_destroy", "clbm_collide_nodes"):
@@ -190,6 +191,15 @@ class Lattice:
         _check(lib().clbm_autotune(self._h, int(steps), ctypes.byref(bx), ctypes.byref(by),
                                    ctypes.byref(npt), ctypes.byref(us)), self._h)
         return dict(block=(bx.value, by.value), npt=npt.value, us_per_step=us.value)
+
+    def set_rates(self, omega) -> None:
+        """Relaxation rates omega_9..omega_18: a sequence of 10, or a dict
+        {j: omega_j} (missing rates stay 1)."""
+        if isinstance(omega, dict):
+            omega = [float(omega.get(j, 1.0)) for j in range(9, 19)]
+        w = np.ascontiguousarray(omega, dtype=np.float64)
+        assert w.shape == (10,)
+        _check(lib().clbm_set_rates(self._h, _dp(w)), self._h)
 
     def set_launch(self, block_x: int, block_y: int, npt: int) -> None:
         _check(lib().clbm_set_launch(self._h, int(block_x), int(block_y), int(npt)), self._h)

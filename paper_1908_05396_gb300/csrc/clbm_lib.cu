@@ -559,6 +559,16 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
   return CLBM_OK;
 }
 
+int clbm_set_rates(clbm_handle h, const double omega[10]) {
+  if (bad(h) || !omega) return fail(h, CLBM_ERR_ARG, "invalid handle or rates");
+  if (h->batch) return fail(h, CLBM_ERR_ARG, "lattice is in a batch: detach it first");
+  for (int k = 0; k < 10; ++k)
+    if (!(omega[k] > 0.0 && omega[k] < 2.0))
+      return fail(h, CLBM_ERR_ARG, "every relaxation rate must lie in (0, 2)");
+  for (int k = 0; k < 10; ++k) h->P.omega_high[k] = omega[k];
+  return CLBM_OK;
+}
+
 int clbm_set_launch(clbm_handle h, int block_x, int block_y, int npt) {
   if (bad(h)) return fail(h, CLBM_ERR_ARG, "invalid handle");
   if (h->in_place && ((npt & TMA_NPT) || (npt & 3) == 2))

@@ -33,6 +33,14 @@ struct CollideConst {
   R nu_min, nu_max;
   int newtonian; // n == 1: omega_nu has a closed form
   int has_force;
+  // The rates omega_9..18 enter only as factors of their own relaxation
+  // brackets (Eqs. collisionkernelg4..g18; the lower-order g^ terms carry no
+  // rate), and omega_9 scales the isotropic part of the strain rate.  They
+  // are folded into the brackets' constants: c9 = -omega_9/126,
+  // c10..c15 = omega_j/8, c16 = omega_16/12, c17 = omega_17/24,
+  // c18 = omega_18/8, cB = 6 omega_9^2 (unit rates give the constants of the
+  // printed forms exactly).
+  R c9, c10, c11, c12, c13, c14, c15, c16, c17, c18, cB;
 };
 
 // Outputs of one collision besides the populations.
@@ -270,23 +278,24 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
   const R m8 = (Dxx - Dzz) - rho * (ux2 - uz2);
   const R m9 = (Dxx + Dyy + Dzz) - drho - rho * (ux2 + uy2 + uz2);
 
-  // gamma_dot^2 = omega^2 A + B from Eq. strainratetensor (omega_zeta = 1):
-  // with q = 1/(2 rho), the traceless part gives
-  // A = 12 q^2 [m7^2 - m7 m8 + m8^2 + 3 (m4^2 + m5^2 + m6^2)], B = 6 q^2 m9^2.
+  // gamma_dot^2 = omega^2 A + B from Eq. strainratetensor (bulk rate
+  // omega_9): with q = 1/(2 rho), the traceless part gives
+  // A = 12 q^2 [m7^2 - m7 m8 + m8^2 + 3 (m4^2 + m5^2 + m6^2)] and the
+  // isotropic part B = 6 omega_9^2 q^2 m9^2.
   const R q2 = R(0.25) * rinv * rinv;
   const R A = R(12) * q2 * (m7 * m7 - m7 * m8 + m8 * m8 + R(3) * (m4 * m4 + m5 * m5 + m6 * m6));
-  const R B = R(6) * q2 * m9 * m9;
+  const R B = R(C.cB) * q2 * m9 * m9;   // 6 omega_9^2 q^2 m9^2
   R gd;
   const R w = omega_nu(C, rho, rinv, A, B, &gd);
 
   // ---- change of moments, Eqs. collisionkernelg4..g18 --------------------
-  // omega_4..8 = w, omega_9..18 = 1 (Sec. 3.1).
+  // omega_4..8 = w (Sec. 3.1); omega_9..18 from the constants above (1 in Sec. 3.1).
   const R g4 = R(-0.25) * w * m4;
   const R g5 = R(-0.25) * w * m5;
   const R g6 = R(-0.25) * w * m6;
   const R g7 = R(-1.0 / 12.0) * w * m7;
   const R g8 = R(-1.0 / 36.0) * w * (R(2) * m8 - m7);
-  const R g9 = R(-1.0 / 126.0) * m9;
+  const R g9 = R(C.c9) * m9;
 
   // g^_10..15 in +/- pairs: with the row sums
   //   Xy = ux k'yy - k'xyy + 2 uy k'xy - 2 rho ux uy^2 (and Xz, Yx, Yz, Zx, Zy
@@ -304,12 +313,12 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
   const R a4y = uy * g4, a5z = uz * g5, a4x = ux * g4, a6z = uz * g6, a5x = ux * g5, a6y = uy * g6;
   const R hx = R(0.75) * ux, hy = R(0.75) * uy, hz = R(1.5) * uz;
   const R w9 = R(14) * g9;
-  const R g10 = R(0.125) * (Xy + Xz) + (a4y + a5z) + hx * (w9 - (g7 + g8));
-  const R g13 = R(0.125) * (Xy - Xz) + (a4y - a5z) + hx * (R(3) * g8 - g7);
-  const R g11 = R(0.125) * (Yx + Yz) + (a4x + a6z) + hy * (w9 + (g7 - g8));
-  const R g14 = R(0.125) * (Yz - Yx) + (a6z - a4x) - hy * (g7 + R(3) * g8);
-  const R g12 = R(0.125) * (Zx + Zy) + (a5x + a6y) + hz * (g8 + R(7) * g9);
-  const R g15 = R(0.125) * (Zx - Zy) + (a5x - a6y) + hz * g7;
+  const R g10 = R(C.c10) * (Xy + Xz) + (a4y + a5z) + hx * (w9 - (g7 + g8));
+  const R g13 = R(C.c13) * (Xy - Xz) + (a4y - a5z) + hx * (R(3) * g8 - g7);
+  const R g11 = R(C.c11) * (Yx + Yz) + (a4x + a6z) + hy * (w9 + (g7 - g8));
+  const R g14 = R(C.c14) * (Yz - Yx) + (a6z - a4x) - hy * (g7 + R(3) * g8);
+  const R g12 = R(C.c12) * (Zx + Zy) + (a5x + a6y) + hz * (g8 + R(7) * g9);
+  const R g15 = R(C.c15) * (Zx - Zy) + (a5x - a6y) + hz * g7;
 
   // Post-collision diagonal central moments k~ii = rho/3 + a_i (the <K g^|e_i^2>
   // rows of Eq. momentscascadedcollisionterm added to k'_ii - rho u_i^2), and
@@ -341,15 +350,15 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
   // shared products: ux uy g4, ux uz g5, uy uz g6 and ux g10, uy g11, uz g12
   const R p4 = ux * a4y, p5 = ux * a5z, p6 = uy * a6z;
   const R v10 = ux * g10, v11 = uy * g11, v12 = uz * g12;
-  const R g16 = R(1.0 / 12.0) * b16 - R(4.0 / 3.0) * (p4 + p5 + p6) +
+  const R g16 = R(C.c16) * b16 - R(4.0 / 3.0) * (p4 + p5 + p6) +
                 R(0.5) * (ux2 - uy2) * g7 + R(0.5) * (ux2 + uy2 - R(2) * uz2) * g8 +
                 (R(-7) * (ux2 + uy2 + uz2) - R(8)) * g9 + R(4.0 / 3.0) * (v10 + v11 + v12);
-  const R g17 = R(1.0 / 24.0) * b17 - R(2.0 / 3.0) * (p4 + p5) + R(4.0 / 3.0) * p6 +
+  const R g17 = R(C.c17) * b17 - R(2.0 / 3.0) * (p4 + p5) + R(4.0 / 3.0) * p6 +
                 R(0.25) * (ux2 - uy2 - R(3) * uz2 - R(2)) * g7 +
                 R(0.25) * (ux2 - R(5) * uy2 + uz2 - R(2)) * g8 +
                 R(1.75) * (R(-2) * ux2 + uy2 + uz2) * g9 + R(2.0 / 3.0) * v10 -
                 third * (v11 + v12) - uy * g14 + uz * g15;
-  const R g18 = R(0.125) * b18 - R(2) * (p4 - p5) +
+  const R g18 = R(C.c18) * b18 - R(2) * (p4 - p5) +
                 R(0.75) * (ux2 - uy2 + uz2 + R(2.0 / 3.0)) * g7 +
                 R(0.75) * (R(-3) * ux2 - uy2 + uz2 - R(2)) * g8 + R(5.25) * (uz2 - uy2) * g9 +
                 (v11 - v12) + R(2) * ux * g13 - uy * g14 - uz * g15;

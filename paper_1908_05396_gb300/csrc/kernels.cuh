@@ -59,6 +59,18 @@ __host__ __device__ __forceinline__ CollideConst<R> make_const(const PhysParams&
   C.nu_max = R(P.nu_max);
   C.newtonian = P.newtonian;
   C.has_force = P.has_force;
+  const double* w = P.omega_high;  // omega_9 .. omega_18
+  C.c9 = R(-w[0] / 126.0);
+  C.c10 = R(0.125 * w[1]);
+  C.c11 = R(0.125 * w[2]);
+  C.c12 = R(0.125 * w[3]);
+  C.c13 = R(0.125 * w[4]);
+  C.c14 = R(0.125 * w[5]);
+  C.c15 = R(0.125 * w[6]);
+  C.c16 = R(w[7] / 12.0);
+  C.c17 = R(w[8] / 24.0);
+  C.c18 = R(0.125 * w[9]);
+  C.cB = R(6.0 * w[0] * w[0]);
   return C;
 }
 

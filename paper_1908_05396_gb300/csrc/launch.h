@@ -34,6 +34,9 @@ struct PhysParams {
   double inv_scale; // storage decode scale (1 except FP16)
   int newtonian;
   int has_force;
+  // relaxation rates omega_9 .. omega_18 (bulk, third and fourth order;
+  // Sec. 3.1 sets them to 1, Sec. 5 notes they may be tuned)
+  double omega_high[10] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
 };
 
 // Work buffers of a check step.

@@ -394,3 +394,67 @@ def test_storage_forms_at_steady_state(clbm):
     # values; its frozen rounding error grows with the lattice (2.7e-3 here,
     # about 1e-2 at 64^3), so F16S only gets a regression bound.
     assert np.linalg.norm(u16 - u64) / n64 <= 5e-3
+
+
+# ---- tunable relaxation rates omega_9..18 (Sec. 3.1, Sec. 5) ------------------
+_RATES = {9: 1.25, 10: 0.7, 11: 1.6, 12: 0.9, 13: 1.4, 14: 0.55, 15: 1.8, 16: 1.1, 17: 0.8,
+          18: 1.5}
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-14), ("f32", 1e-6)])
+def test_tuned_rates_one_step_vs_oracle(clbm, oracle, dtype, tol):
+    # distinct rates on the ragged mixed lattice (walls, lid, periodic z,
+    # force), one step from a random state, every node against the oracle
+    p = _oracle_params(oracle, _MIXED)
+    p.omega_high = dict(_RATES)
+    r = wl.noise((19, _MIXED.nz, _MIXED.ny, _MIXED.nx), seed=21, amp=0.05)
+    with _lattice(clbm, _MIXED, dtype) as lat:
+        lat.set_rates(_RATES)
+        rest = lat.get_state()
+        lat.set_state(rest * (1 + r))
+        lat.step(1)
+        f_gpu = lat.get_state()
+    w = oracle.weights()
+    f0 = oracle.rest_state(p) * (1 + r)
+    f0 = _round_dev(f0.reshape(19, -1), w, dtype).reshape(f0.shape)
+    f_ref = oracle.run(p, f0, 1)
+    assert np.abs(f_gpu - f_ref).max() <= tol
+
+
+# milder distinct rates for a long run (the ones above make this cavity
+# unstable in the oracle as well)
+_RATES_LONG = {9: 1.1, 10: 1.2, 11: 0.9, 12: 1.3, 13: 1.0, 14: 1.15, 15: 0.95, 16: 1.25,
+               17: 1.05, 18: 1.35}
+
+
+def test_tuned_rates_cavity_f64_1000_steps(clbm, oracle):
+    prob = wl.cavity(32, 100.0, 0.7)
+    p = _oracle_params(oracle, prob)
+    p.omega_high = dict(_RATES_LONG)
+    f_ref = oracle.run(p, oracle.rest_state(p), 1000)
+    _, u_ref, _ = oracle.fields(p, f_ref)
+    with _lattice(clbm, prob, "f64") as lat, _lattice(clbm, prob, "f64") as unit:
+        lat.set_rates([_RATES_LONG[j] for j in range(9, 19)])
+        lat.step(1000)
+        unit.step(1000)
+        _, u, _ = lat.fields()
+        _, u1, _ = unit.fields()
+    assert np.all(np.isfinite(u_ref))
+    assert np.abs(u - u_ref).max() / 0.05 <= 1e-10
+    assert np.abs(u1 - u_ref).max() > 1e-4      # the rates matter
+
+
+def test_unit_rates_change_nothing_and_bad_rates_are_rejected(clbm):
+    prob = wl.cavity(24, 100.0, 0.8)
+    with _lattice(clbm, prob, "f32") as a, _lattice(clbm, prob, "f32") as b:
+        b.set_rates([1.0] * 10)
+        a.step(120)
+        b.step(120)
+        assert np.array_equal(a.get_state(), b.get_state())
+        for bad in ([1.0] * 9 + [2.0], [0.0] + [1.0] * 9, [float("nan")] * 10):
+            with pytest.raises(clbm.CLBMError):
+                b.set_rates(bad)
+        with clbm.Batch("f32", capacity=2) as batch:
+            batch.add(b)
+            with pytest.raises(clbm.CLBMError):
+                b.set_rates([1.2] * 10)
