@@ -624,6 +624,50 @@ def run_precision(args):
     return 0
 
 
+STABILITY_RATES = {
+    "unit": None,                                   # Sec. 3.1: omega_9..18 = 1
+    "w9=0.5": (0.5,) + (1.0,) * 9,                  # larger bulk viscosity
+    "w9=1.5": (1.5,) + (1.0,) * 9,
+    "w10-18=0.8": (1.0,) + (0.8,) * 9,              # under-relaxed 3rd/4th orders
+    "w10-18=1.2": (1.0,) + (1.2,) * 9,              # over-relaxed 3rd/4th orders
+}
+
+
+def run_stability(args):
+    """Stability limit of the cascaded scheme alone (Sec. 5, second study):
+    the largest lid velocity a 64^3 cavity sustains for 50,000 steps, for
+    n = 0.8, 1, 1.5, several tau_p and several sets of the rates omega_9..18,
+    by bisection with all open cases of a round in one batch.  With
+    --stability-confirm the FP64 form re-runs each bracket of the unit-rate
+    set at tau_p = 0.51 (the stable and the unstable end)."""
+    import torch  # noqa: F401  (CUDA context on the chosen device)
+    from paper_1908_05396_gb300 import build
+    build.build()
+    from paper_1908_05396_gb300 import stability as st
+    cases = [st.Case(n, tau, rates, label) for label, rates in STABILITY_RATES.items()
+             for n in (0.8, 1.0, 1.5) for tau in args.stability_tau]
+    t0 = time.perf_counter()
+    run = st.batch_runner(args.stability_L, args.stability_steps, args.stability_dtype)
+    res = st.max_lid_velocity(cases, run, u_hi=args.stability_uhi, rounds=args.stability_rounds)
+    sec = time.perf_counter() - t0
+    out = {"metric": "max stable lid velocity", "L": args.stability_L,
+           "steps": args.stability_steps, "dtype": args.stability_dtype,
+           "u_hi": args.stability_uhi, "rounds": args.stability_rounds, "seconds": sec,
+           "cases": [{"rates": c.label, "n": c.n, "tau_p": c.tau_p, "u_stable": lo,
+                      "u_unstable": hi} for c, (lo, hi) in zip(cases, res)]}
+    if args.stability_confirm:
+        sel = [(c, r) for c, r in zip(cases, res)
+               if c.label == "unit" and c.tau_p == 0.51 and r[1] is not None]
+        pairs = [(c, u) for c, (lo, hi) in sel for u in (lo, hi) if u > 0.0]
+        t0 = time.perf_counter()
+        ok = st.batch_runner(args.stability_L, args.stability_steps, "f64")(
+            [c for c, _ in pairs], [u for _, u in pairs])
+        out["f64_confirm"] = {"seconds": time.perf_counter() - t0, "runs": [
+            {"n": c.n, "tau_p": c.tau_p, "U": u, "stable": s} for (c, u), s in zip(pairs, ok)]}
+    print(json.dumps(out))
+    return 0
+
+
 def run_profile_batch(args):
     """The batch profiling case: the 64 seeded cavities in one FP32 batch."""
     import torch
@@ -706,6 +750,17 @@ def main():
                     choices=["f64", "f32", "f16s"],
                     help="time only the steps of the n=0.5 cavity in one storage form "
                          "(profiling case)")
+    ap.add_argument("--stability", action="store_true",
+                    help="largest stable lid velocity of the cavity per (n, tau_p, rates)")
+    ap.add_argument("--stability-L", type=int, default=64)
+    ap.add_argument("--stability-steps", type=int, default=50_000)
+    ap.add_argument("--stability-tau", type=float, nargs="*", default=[0.505, 0.51, 0.52, 0.55])
+    ap.add_argument("--stability-uhi", type=float, default=0.25,
+                    help="upper end of the bisection (the library takes |U_lid| < 0.3)")
+    ap.add_argument("--stability-rounds", type=int, default=8)
+    ap.add_argument("--stability-dtype", default="f32", choices=["f64", "f32"])
+    ap.add_argument("--stability-confirm", action="store_true",
+                    help="re-run the unit-rate brackets at tau_p = 0.51 in FP64")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -715,6 +770,8 @@ def main():
         return run_profile_batch(args)
     if args.precision:
         return run_precision(args)
+    if args.stability:
+        return run_stability(args)
     if args.profile:
         return run_profile(args)
     return run_ours(args)
