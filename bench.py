@@ -408,17 +408,25 @@ def _batch_bench(clbm, torch, wl, steps, peak):
     probs = wl.batch_cavities(count=64, seed=0)
     lats = [clbm.Lattice(**p.kwargs(), dtype="f32") for p in probs]
     N = sum(p.N for p in probs)
-    with clbm.Batch("f32", capacity=len(lats), check_interval=100) as b:
-        for lt in lats:
-            b.add(lt)
-        tuned = b.autotune(4)
+    def timed(b):
         b.step(200)                          # warm-up: graph capture and caches
         b.sync()
         t0 = time.perf_counter()
         b.step(steps)
         b.sync()
-        dt = time.perf_counter() - t0
+        return time.perf_counter() - t0
+
+    with clbm.Batch("f32", capacity=len(lats), check_interval=100) as b:
+        for lt in lats:
+            b.add(lt)
+        tuned = b.autotune(4)
+        dt = timed(b)
         diverged = sum(1 for s in range(len(lats)) if b.stats(s)["diverged"])
+        # both modes at their usual best shapes, whichever the tuner kept
+        b.set_launch(32, 4, 2, -8)
+        dt_persistent = timed(b)
+        b.set_lattice_launch(32, 2, 5, 4)
+        dt_per_lattice = timed(b)
     mlups = N * steps / dt / 1e6
     # the same lattices, one launch per lattice per step
     for lt in lats:
@@ -438,6 +446,10 @@ def _batch_bench(clbm, torch, wl, steps, peak):
     return {"workload": "64 cavities, L~U{32..96}, Re~U[50,500], n~U[0.4,1.6], U=0.05, FP32, seed 0",
             "nodes": N, "steps": steps, "MLUPS": mlups, "GB/s": gbs, "frac_of_hbm": gbs / peak,
             "launch": tuned, "diverged_lattices": diverged,
+            "persistent_MLUPS": N * steps / dt_persistent / 1e6,
+            "persistent_launch": "one persistent launch per step: 32x4 tiles, zc 2, 8 capped CTAs/SM",
+            "per_lattice_MLUPS": N * steps / dt_per_lattice / 1e6,
+            "per_lattice_launch": "one launch per lattice per step: 32x2 capped, 4 streams",
             "separate_launches_MLUPS": N * n_alone / dt_alone / 1e6,
             "timing": "host wall clock around graph-captured batch steps, synchronised"}
 

@@ -192,7 +192,8 @@ int clbm_set_rates(clbm_handle h, const double omega[10]);
  * Not in the paper: a batch steps up to `capacity` lattices of one storage
  * form (any of the four, F16R with its reference moments) together, one launch of a persistent kernel per time step for all of
  * them (tiles of every lattice from a device-side table), with each whole
- * check interval queued as one CUDA graph.  Lattices join and leave between
+ * check interval queued as one CUDA graph (or, after
+ * clbm_batch_set_lattice_launch, one launch per lattice within that graph).  Lattices join and leave between
  * clbm_batch_step() calls; each keeps its own buffers, parameters, step
  * count and residual.  While a lattice is in a batch, clbm_step() on it
  * fails; clbm_fields/get_state/residual/... on it first wait for the batch.
@@ -223,9 +224,24 @@ int clbm_batch_stats(clbm_batch b, int slot, double* residual, double* mass, int
  * tile zc >= 1, resident blocks per SM of the persistent grid (negative:
  * the same count with the register-capped kernel variant). */
 int clbm_batch_set_launch(clbm_batch b, int block_x, int block_y, int zc, int blocks_per_sm);
-/* Time block shapes x zc x blocks-per-SM x register cap on the attached
- * lattices (states saved and restored) and keep the fastest; *blocks_per_sm
- * is negative when the capped variant won. */
+/* One launch per lattice instead of the persistent kernel (FP64, FP32,
+ * F16S; CLBM_ERR_UNSUPPORTED for F16R, whose rounding is seeded by the batch's
+ * device-side step count): every step launches each attached lattice's own
+ * step kernel (block_x x block_y threads, a multiple of 32 and <= 256; npt 1,
+ * or 5 for the register-capped kernel), the lattices spread over `streams`
+ * (1..16) streams, largest first onto the least-loaded one.  The streams fork
+ * from the batch's stream and join it around each check interval, which is
+ * still one CUDA graph; a change of membership recaptures it.  Results are
+ * those of clbm_step on each lattice.  clbm_batch_set_launch() returns to the
+ * persistent kernel. */
+int clbm_batch_set_lattice_launch(clbm_batch b, int block_x, int block_y, int npt, int streams);
+/* Time block shapes x zc x blocks-per-SM x register cap of the persistent
+ * kernel and, except for F16R, block shapes x kernel variant x streams of one
+ * launch per lattice, on the attached lattices (states saved and restored),
+ * and keep the fastest.  Persistent kernel: *blocks_per_sm is negative when
+ * the capped variant won.  One launch per lattice: *zc is 0, *block_x and
+ * *block_y are the lattices' block, |*blocks_per_sm| is the stream count,
+ * negative for the register-capped kernel. */
 int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int* zc,
                         int* blocks_per_sm, double* us_per_step);
 int clbm_batch_sync(clbm_batch b);

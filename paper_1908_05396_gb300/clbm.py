@@ -295,6 +295,8 @@ class Batch:
                                            ctypes.POINTER(ctypes.c_int64)]
             L.clbm_batch_set_launch.argtypes = [B, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.c_int]
+            L.clbm_batch_set_lattice_launch.argtypes = [B, ctypes.c_int, ctypes.c_int,
+                                                        ctypes.c_int, ctypes.c_int]
             L.clbm_batch_autotune.argtypes = [B, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4 + [_D]
             L.clbm_batch_sync.argtypes = [B]
             L.clbm_batch_destroy.argtypes = [B]
@@ -302,6 +304,7 @@ class Batch:
             L.clbm_batch_last_error.restype = ctypes.c_char_p
             for n in ("clbm_batch_create", "clbm_batch_add", "clbm_batch_remove", "clbm_batch_detach",
                       "clbm_batch_step", "clbm_batch_stats", "clbm_batch_set_launch",
+                      "clbm_batch_set_lattice_launch",
                       "clbm_batch_autotune", "clbm_batch_sync", "clbm_batch_destroy"):
                 getattr(L, n).restype = ctypes.c_int
             L._batch_ready = True
@@ -339,16 +342,35 @@ class Batch:
         return dict(residual=R.value, mass=m.value, diverged=bool(dv.value), steps=st.value)
 
     def set_launch(self, block_x, block_y, zc, blocks_per_sm) -> None:
+        """The persistent kernel with this launch shape."""
         self._bcheck(lib().clbm_batch_set_launch(self._b, int(block_x), int(block_y), int(zc),
                                                  int(blocks_per_sm)))
 
+    def set_lattice_launch(self, block_x, block_y, npt, streams) -> None:
+        """One launch of each lattice's own step kernel per step, on `streams` streams."""
+        self._bcheck(lib().clbm_batch_set_lattice_launch(self._b, int(block_x), int(block_y),
+                                                         int(npt), int(streams)))
+
     def autotune(self, steps: int = 6) -> dict:
+        """Time the launch choices and keep the fastest; the returned dict
+        can be given back to ``apply_launch``."""
         v = [ctypes.c_int() for _ in range(4)]
         us = ctypes.c_double()
         self._bcheck(lib().clbm_batch_autotune(self._b, int(steps), *[ctypes.byref(x) for x in v],
                                                ctypes.byref(us)))
-        return dict(block=(v[0].value, v[1].value), zc=v[2].value, blocks_per_sm=v[3].value,
-                    us_per_step=us.value)
+        if v[2].value == 0:
+            return dict(mode="per_lattice", block=(v[0].value, v[1].value),
+                        npt=5 if v[3].value < 0 else 1, streams=abs(v[3].value),
+                        us_per_step=us.value)
+        return dict(mode="persistent", block=(v[0].value, v[1].value), zc=v[2].value,
+                    blocks_per_sm=v[3].value, us_per_step=us.value)
+
+    def apply_launch(self, info: dict) -> None:
+        """Set the launch an ``autotune`` result describes."""
+        if info["mode"] == "per_lattice":
+            self.set_lattice_launch(*info["block"], info["npt"], info["streams"])
+        else:
+            self.set_launch(*info["block"], info["zc"], info["blocks_per_sm"])
 
     def sync(self) -> None:
         self._bcheck(lib().clbm_batch_sync(self._b))

@@ -8,6 +8,13 @@
 // memory.  The kernel reads its tile table and lattice descriptors from device
 // memory, so the graph stays valid when lattices join or leave; only a change
 // of launch shape or of the table's capacity recaptures it.
+//
+// A second mode launches every lattice's own step kernel (kernels.cuh) once
+// per step instead, the lattices spread over a few streams that fork from the
+// batch's stream at the start of a check interval and join it at the end.
+// Each lattice then runs with its parameters as kernel arguments and no tile
+// table, and the streams fill each other's tails.  Its graph holds the
+// lattices' buffer addresses, so a change of membership recaptures it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,6 +62,13 @@ struct clbm_batch_ctx {
   int blocks_per_sm = 4;
   bool cap = false;                   // register-capped kernel variant
   int sms = 1;
+  int mode = 0;                       // 0: persistent kernel; 1: one launch per lattice
+  dim3 pl_block{32, 2, 1};            // mode 1: block of every lattice's step kernel
+  int pl_npt = 5;                     // mode 1: 1, or 5 for the register-capped kernel
+  int pl_streams = 4;                 // mode 1: streams the lattices are spread over
+  std::vector<cudaStream_t> aux;      // mode 1: the streams besides `stream`
+  std::vector<cudaEvent_t> ev;        // mode 1: fork event, then one join event per aux stream
+  std::vector<int> stream_of;         // mode 1: slot -> stream (0 is `stream`)
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t check_done = nullptr;
   std::string err;
@@ -165,6 +179,97 @@ void drop_graph(clbm_batch_ctx* b) {
   b->graph = nullptr;
 }
 
+// ---- mode 1: one launch per lattice --------------------------------------
+
+cudaStream_t pl_stream(const clbm_batch_ctx* b, int k) {
+  return k == 0 ? b->stream : b->aux[size_t(k - 1)];
+}
+
+// Create the extra streams and the fork/join events that `streams` needs.
+cudaError_t ensure_streams(clbm_batch_ctx* b, int streams) {
+  while (int(b->aux.size()) < streams - 1) {
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    b->aux.push_back(st);
+  }
+  while (int(b->ev.size()) < streams) {
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    b->ev.push_back(ev);
+  }
+  return cudaSuccess;
+}
+
+// Spread the lattices over the streams: largest first, each onto the stream
+// with the fewest nodes so far.
+void assign_streams(clbm_batch_ctx* b) {
+  std::vector<int> order;
+  for (int s = 0; s < b->capacity; ++s)
+    if (b->slots[s]) order.push_back(s);
+  auto nodes = [b](int s) {
+    const clbm_ctx* h = b->slots[size_t(s)];
+    return double(h->g.nx) * h->g.ny * h->g.nz;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return nodes(a) > nodes(c); });
+  std::vector<double> load(size_t(b->pl_streams), 0.0);
+  b->stream_of.assign(size_t(b->capacity), 0);
+  for (int s : order) {
+    const size_t k = size_t(std::min_element(load.begin(), load.end()) - load.begin());
+    b->stream_of[size_t(s)] = int(k);
+    load[k] += nodes(s);
+  }
+}
+
+// The extra streams wait for everything queued on `stream` so far.
+cudaError_t fork_streams(clbm_batch_ctx* b) {
+  cudaError_t e = cudaEventRecord(b->ev[0], b->stream);
+  for (int k = 1; k < b->pl_streams && e == cudaSuccess; ++k)
+    e = cudaStreamWaitEvent(b->aux[size_t(k - 1)], b->ev[0], 0);
+  return e;
+}
+
+// `stream` waits for everything queued on the extra streams so far.
+cudaError_t join_streams(clbm_batch_ctx* b) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 1; k < b->pl_streams && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(b->ev[size_t(k)], b->aux[size_t(k - 1)]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev[size_t(k)], 0);
+  }
+  return e;
+}
+
+// One step of every lattice, each on its stream.  `flip` = 1 when the state
+// sits in the other buffer than h->cur says (inside a captured interval).
+// The check sums of slot s go to the batch's row s, as in mode 0.
+cudaError_t launch_lattices(clbm_batch_ctx* b, bool check, int flip) {
+  for (int s = 0; s < b->capacity; ++s) {
+    clbm_ctx* h = b->slots[size_t(s)];
+    if (!h) continue;
+    double* acc = b->d_acc + 4 * size_t(s);
+    CheckBufs cb{h->uprev, acc, reinterpret_cast<int*>(acc + 3)};
+    const int c = h->cur ^ flip;
+    const void* src = h->buf[c];
+    void* dst = h->buf[1 - c];
+    const cudaStream_t st = pl_stream(b, b->stream_of[size_t(s)]);
+    cudaError_t e;
+    switch (b->dtype) {
+      case CLBM_F64:
+        e = launch_step_f64(src, dst, h->g, h->P, cb, check, b->pl_block, b->pl_npt, st);
+        break;
+      case CLBM_F32:
+        e = launch_step_f32(src, dst, h->g, h->P, cb, check, b->pl_block, b->pl_npt, st);
+        break;
+      default:
+        e = launch_step_f16(src, dst, h->g, h->P, cb, check, b->pl_block, b->pl_npt, st);
+        break;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Rebuild and upload the tables from the attached lattices' current state.
 int upload(clbm_batch_ctx* b) {
   BCK(b, cudaStreamSynchronize(b->stream));  // staging buffers and tables are free
@@ -217,6 +322,10 @@ int upload(clbm_batch_ctx* b) {
                       cudaMemcpyHostToDevice));
   }
   BCK(b, cudaMemcpy(b->d_hdr, &hdr, sizeof(hdr), cudaMemcpyHostToDevice));
+  if (b->mode == 1) {
+    assign_streams(b);
+    drop_graph(b);  // the graph holds the lattices' buffer addresses
+  }
   b->parity = 0;
   b->dirty = false;
   return CLBM_OK;
@@ -235,7 +344,13 @@ void advance(clbm_batch_ctx* b, int64_t n) {
 int one_step(clbm_batch_ctx* b) {
   const bool check = ((b->steps + 1) % b->check_interval) == 0;
   if (check) BCK(b, cudaMemsetAsync(b->d_acc, 0, size_t(b->capacity) * 4 * sizeof(double), b->stream));
-  BCK(b, launch(b, check));
+  if (b->mode == 1) {
+    BCK(b, fork_streams(b));
+    BCK(b, launch_lattices(b, check, 0));
+    BCK(b, join_streams(b));
+  } else {
+    BCK(b, launch(b, check));
+  }
   b->parity ^= 1;
   if (check) {
     BCK(b, cudaMemcpyAsync(b->h_acc, b->d_acc, size_t(b->capacity) * 4 * sizeof(double),
@@ -254,8 +369,21 @@ int capture(clbm_batch_ctx* b) {
   cudaGraph_t g = nullptr;
   BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
+  if (b->mode == 1) {
+    // Only the last step's check writes the sums: clear them up front, so
+    // that the streams stay forked for the whole interval.
+    e = cudaMemsetAsync(b->d_acc, 0, size_t(b->capacity) * 4 * sizeof(double), b->stream);
+    if (e == cudaSuccess) e = fork_streams(b);
+    for (int k = 0; k < b->check_interval && e == cudaSuccess; ++k)
+      e = launch_lattices(b, k == b->check_interval - 1, k & 1);
+    if (e == cudaSuccess) e = join_streams(b);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->h_acc, b->d_acc, size_t(b->capacity) * 4 * sizeof(double),
+                          cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->check_done, b->stream);
+  }
   int par = 0;
-  for (int k = 0; k < b->check_interval && e == cudaSuccess; ++k) {
+  for (int k = 0; k < b->check_interval && e == cudaSuccess && b->mode == 0; ++k) {
     const bool check = k == b->check_interval - 1;
     if (check)
       e = cudaMemsetAsync(b->d_acc, 0, size_t(b->capacity) * 4 * sizeof(double), b->stream);
@@ -442,6 +570,27 @@ int clbm_batch_set_launch(clbm_batch b, int block_x, int block_y, int zc, int bl
   b->zc = zc;
   b->blocks_per_sm = blocks_per_sm;
   b->cap = cap;
+  b->mode = 0;
+  b->dirty = true;
+  drop_graph(b);
+  return CLBM_OK;
+}
+
+int clbm_batch_set_lattice_launch(clbm_batch b, int block_x, int block_y, int npt, int streams) {
+  if (!valid(b)) return bfail(b, CLBM_ERR_ARG, "invalid batch");
+  if (b->dtype == CLBM_F16R)
+    return bfail(b, CLBM_ERR_UNSUPPORTED,
+                 "F16R batches take the persistent kernel (its rounding is seeded by the step)");
+  if (block_x < 1 || block_y < 1 || block_x * block_y > 256 || (block_x * block_y) % 32 ||
+      (npt != 1 && npt != 5) || streams < 1 || streams > 16)
+    return bfail(b, CLBM_ERR_ARG, "bad launch shape");
+  BCK(b, cudaSetDevice(b->device));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  BCK(b, ensure_streams(b, streams));
+  b->pl_block = dim3(block_x, block_y, 1);
+  b->pl_npt = npt;
+  b->pl_streams = streams;
+  b->mode = 1;
   b->dirty = true;
   drop_graph(b);
   return CLBM_OK;
@@ -491,6 +640,7 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
       for (int bp : bpss) {
         if (err != cudaSuccess) break;
         if (sh[0] * sh[1] * bp > 2048) continue;   // at most 2048 threads per SM
+        b->mode = 0;
         b->cap = capped != 0;
         b->block = dim3(sh[0], sh[1], 1);
         b->zc = z;
@@ -519,6 +669,50 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
           bc = capped != 0;
         }
       }
+  // One launch per lattice (not for F16R): block x kernel variant x streams.
+  int bmode = 0, pbx = 32, pby = 2, pnpt = 5, pst = 4;
+  if (b->dtype != CLBM_F16R) {
+    const int pshapes[][2] = {{32, 2}, {32, 4}, {64, 2}};
+    const int pnpts[] = {5, 1};
+    const int pstreams[] = {2, 4, 8};
+    if (err == cudaSuccess) err = ensure_streams(b, 8);
+    for (auto& sh : pshapes)
+      for (int np : pnpts)
+        for (int ns : pstreams) {
+          if (err != cudaSuccess) break;
+          b->mode = 1;
+          b->pl_block = dim3(sh[0], sh[1], 1);
+          b->pl_npt = np;
+          b->pl_streams = ns;
+          b->dirty = true;
+          if (upload(b) != CLBM_OK) { err = cudaErrorUnknown; break; }
+          err = fork_streams(b);
+          for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
+            err = launch_lattices(b, false, b->parity);
+            b->parity ^= 1;
+          }
+          if (err == cudaSuccess) err = join_streams(b);
+          if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
+          if (err == cudaSuccess) err = fork_streams(b);
+          for (int k = 0; k < steps && err == cudaSuccess; ++k) {
+            err = launch_lattices(b, false, b->parity);
+            b->parity ^= 1;
+          }
+          if (err == cudaSuccess) err = join_streams(b);
+          if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
+          if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+          float ms = 0.0f;
+          if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+          if (err == cudaSuccess && 1e3 * ms / steps < best) {
+            best = 1e3 * ms / steps;
+            bmode = 1;
+            pbx = sh[0];
+            pby = sh[1];
+            pnpt = np;
+            pst = ns;
+          }
+        }
+  }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   // Restore states, counters and the chosen shape.
@@ -542,16 +736,29 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
   b->zc = bz;
   b->blocks_per_sm = bb;
   b->cap = bc;
+  b->mode = bmode;
+  b->pl_block = dim3(pbx, pby, 1);
+  b->pl_npt = pnpt;
+  b->pl_streams = pst;
   b->dirty = true;
   drop_graph(b);
   cudaError_t e3 = cudaStreamSynchronize(b->stream);
   if (err == cudaSuccess) err = e3;
   if (err != cudaSuccess)
     return bfail(b, CLBM_ERR_CUDA, std::string("clbm_batch_autotune: ") + cudaGetErrorString(err));
-  if (block_x) *block_x = bx;
-  if (block_y) *block_y = by;
-  if (zc) *zc = bz;
-  if (blocks_per_sm) *blocks_per_sm = bc ? -bb : bb;  // negative: register-capped variant
+  if (bmode == 1) {
+    // zc = 0: one launch per lattice; |blocks_per_sm| = streams, negative
+    // for the register-capped kernel
+    if (block_x) *block_x = pbx;
+    if (block_y) *block_y = pby;
+    if (zc) *zc = 0;
+    if (blocks_per_sm) *blocks_per_sm = pnpt == 5 ? -pst : pst;
+  } else {
+    if (block_x) *block_x = bx;
+    if (block_y) *block_y = by;
+    if (zc) *zc = bz;
+    if (blocks_per_sm) *blocks_per_sm = bc ? -bb : bb;  // negative: register-capped variant
+  }
   if (us_per_step) *us_per_step = best;
   return CLBM_OK;
 }
@@ -579,6 +786,8 @@ int clbm_batch_destroy(clbm_batch b) {
   if (b->h_acc) cudaFreeHost(b->h_acc);
   if (b->h_stage) cudaFreeHost(b->h_stage);
   if (b->check_done) cudaEventDestroy(b->check_done);
+  for (cudaEvent_t ev : b->ev) cudaEventDestroy(ev);
+  for (cudaStream_t st : b->aux) cudaStreamDestroy(st);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return CLBM_OK;

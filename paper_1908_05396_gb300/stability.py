@@ -68,7 +68,7 @@ def batch_runner(L: int = 64, steps: int = 50_000, dtype: str = "f32",
                 if autotune and not launch:
                     launch.update(b.autotune())
                 elif launch:
-                    b.set_launch(*launch["block"], launch["zc"], launch["blocks_per_sm"])
+                    b.apply_launch(launch)
                 done = 0
                 while done < steps and slots:
                     k = min(chunk, steps - done)

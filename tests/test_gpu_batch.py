@@ -1,7 +1,8 @@
 """Batched stepping: many uneven lattices in one persistent launch must give
 the same result as each lattice stepped alone (same storage form), including
 lattices that join and leave while others run, and the per-lattice residuals
-of the batch's check steps must match the lone lattices'.
+of the batch's check steps must match the lone lattices'.  The same holds for
+the batch's second mode, one launch per lattice on several streams.
 
 FP64 results are bitwise identical.  The FP32-math forms agree to FP32
 rounding (nvcc may fuse a different set of multiply-adds in the batch
@@ -51,18 +52,29 @@ def _same(f, f_ref, dtype):
         assert np.all(np.abs(f - f_ref) <= dev * 2.0 ** -10 + 1e-7)
 
 
+def _set_mode(b, mode):
+    if mode == "per_lattice":
+        b.set_lattice_launch(32, 2, 5, 3)
+
+
+@pytest.mark.parametrize("mode", ["persistent", "per_lattice"])
 @pytest.mark.parametrize("dtype", ["f64", "f32", "f16s", "f16r"])
-def test_batch_equals_alone(clbm, dtype):
+def test_batch_equals_alone(clbm, dtype, mode):
+    if mode == "per_lattice" and dtype == "f16r":
+        pytest.skip("F16R batches take the persistent kernel")
     probs = _mix()
     steps = 257                      # graph chunks + single steps + odd count
     alone = []
     for p in probs:
         with clbm.Lattice(**p.kwargs(), dtype=dtype, check_interval=50) as lat:
+            if mode == "per_lattice":
+                lat.set_launch(32, 2, 5)       # the kernel the batch launches: bitwise FP64
             lat.step(steps)
             R, _ = lat.residual()
             alone.append((lat.get_state(), R, lat.mass()))
     lats = [clbm.Lattice(**p.kwargs(), dtype=dtype, check_interval=50) for p in probs]
     with clbm.Batch(dtype, capacity=8, check_interval=50) as b:
+        _set_mode(b, mode)
         slots = [b.add(lt) for lt in lats]
         b.step(steps)
         for s, lt, (f_ref, R_ref, m_ref) in zip(slots, lats, alone):
@@ -77,11 +89,13 @@ def test_batch_equals_alone(clbm, dtype):
         lt.close()
 
 
-def test_batch_join_and_leave(clbm):
+@pytest.mark.parametrize("mode", ["persistent", "per_lattice"])
+def test_batch_join_and_leave(clbm, mode):
     probs = _mix(1)
     counts = {}
     lats = [clbm.Lattice(**p.kwargs(), dtype="f32", check_interval=50) for p in probs]
     with clbm.Batch("f32", capacity=4, check_interval=50) as b:
+        _set_mode(b, mode)
         s0 = b.add(lats[0])
         s1 = b.add(lats[1])
         b.step(120)
@@ -115,13 +129,35 @@ def test_batch_autotune_restores_state(clbm):
         b.step(30)
         before = [lt.get_state() for lt in lats]
         info = b.autotune(3)
-        assert info["us_per_step"] > 0 and info["zc"] >= 1
+        assert info["us_per_step"] > 0
+        assert info["mode"] == "per_lattice" or info["zc"] >= 1
         after = [lt.get_state() for lt in lats]
         for x, y in zip(before, after):
             assert np.array_equal(x, y)
         assert all(lt.steps_done() == 30 for lt in lats)
-    for lt in lats:
+        # the kept launch steps on correctly, whichever mode won
+        b.step(70)
+        b.apply_launch(info)
+        b.step(1)
+    for lt, p in zip(lats, probs):
+        with clbm.Lattice(**p.kwargs(), dtype="f32") as ref:
+            ref.step(101)
+            _same(lt.get_state(), ref.get_state(), "f32")
         lt.close()
+
+
+def test_lattice_launch_limits(clbm):
+    lat = clbm.Lattice(**wl.cavity(10, 100.0, 1.0).kwargs(), dtype="f16r")
+    with clbm.Batch("f16r", capacity=2) as b:
+        with pytest.raises(clbm.CLBMError):
+            b.set_lattice_launch(32, 2, 5, 2)
+        b.add(lat)
+        assert b.autotune(2)["mode"] == "persistent"
+    with clbm.Batch("f32", capacity=2) as b:
+        for bad in ((24, 2, 5, 2), (32, 2, 2, 2), (32, 2, 5, 0), (32, 2, 5, 17), (512, 1, 1, 2)):
+            with pytest.raises(clbm.CLBMError):
+                b.set_lattice_launch(*bad)
+    lat.close()
 
 
 def test_step_refused_while_batched(clbm):
