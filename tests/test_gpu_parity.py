@@ -147,6 +147,47 @@ def test_channel_f64_1000_steps(clbm, oracle):
     assert np.abs(gd_gpu - gd_ref).max() <= 1e-10 * gd_ref.max()
 
 
+@pytest.mark.parametrize("n", [0.5, 1.0, 1.5])
+def test_full_size_cavity_fp32_tracks_fp64(clbm, n):
+    # The benchmark lattice (128^3, Re 100) in the benchmark's FP32 launch,
+    # 2000 steps from rest, against the FP64 form (pinned to the oracle
+    # above): the FP32 velocity bar, the cavity's mirror symmetry about the
+    # mid-z plane (the lid moves along x: u_x, u_y even, u_z odd) and mass.
+    prob = wl.cavity(128, 100.0, n)
+    U = prob.U_lid[0]
+    with _lattice(clbm, prob, "f64") as a, _lattice(clbm, prob, "f32") as b:
+        b.set_launch(32, 2, 5)
+        m0 = float(prob.N)                 # rest state, rho0 = 1
+        a.step(2000)
+        b.step(2000)
+        _, ua, _ = a.fields()
+        _, ub, _ = b.fields()
+        ma, mb = a.mass(), b.mass()
+    assert np.linalg.norm(ub - ua) / np.linalg.norm(ua) <= 1e-4
+    for u, tol in ((ua, 1e-12), (ub, 1e-5)):
+        m = u[:, ::-1]
+        assert np.abs(u[0] - m[0]).max() <= tol * U
+        assert np.abs(u[1] - m[1]).max() <= tol * U
+        assert np.abs(u[2] + m[2]).max() <= tol * U
+    assert abs(ma - m0) <= 1e-12 * m0 and abs(mb - m0) <= 1e-6 * m0
+
+
+def test_channel_configuration_f64_20000_steps(clbm, oracle):
+    # The channel configuration at its full size and step count: 4 x 64 x 4,
+    # n = 0.5, G = 1e-6, 20,000 steps from rest.  (Still a transient: the
+    # profile is about half developed; the steady state against the analytic
+    # profile is tested in test_gpu_validation.)
+    prob = wl.channel(64, 0.5, u_max=0.02, G=1e-6)
+    p = _oracle_params(oracle, prob)
+    with _lattice(clbm, prob, "f64") as lat:
+        lat.step(20000)
+        _, u_gpu, _ = lat.fields()
+    f_ref = oracle.run(p, oracle.rest_state(p), 20000)
+    _, u_ref, _ = oracle.fields(p, f_ref)
+    assert np.abs(u_ref).max() > 0.01
+    assert np.abs(u_gpu - u_ref).max() / 0.02 <= 1e-10
+
+
 _MIXED = wl.Problem("mixed", 33, 17, 9, (wl.WALL, wl.WALL, wl.WALL, wl.LID, wl.PERIODIC, wl.PERIODIC),
                     K=0.01, n=0.7, U_lid=(0.04, 0.0, 0.02), body_force=(1e-5, 0.0, -2e-6))
 
@@ -216,15 +257,20 @@ def test_autotune_restores_state_and_keeps_parity(clbm):
 @pytest.mark.parametrize("dtype,launch", [("f64", None), ("f32", None), ("f16s", None),
                                           ("f16r", None), ("f32", (64, 4, 16)),
                                           ("f32", (32, 8, 80)), ("f32", (64, 2, 208)),
-                                          ("f16s", (64, 4, 16)), ("f16s", (64, 2, 208))])
+                                          ("f16s", (64, 4, 16)), ("f16s", (64, 2, 208)),
+                                          ("f32", (32, 2, 5)), ("f16s", (32, 4, 5)),
+                                          ("f32", "in_place"), ("f16s", "in_place"),
+                                          ("f64", "in_place")])
 def test_full_size_cavity_one_step(clbm, oracle, dtype, launch):
     # 128^3 cavity (the benchmark lattice): one step from a random perturbed
-    # state, every node compared with the oracle.
+    # state, every node compared with the oracle; (32, 2, 5) and (32, 4, 5)
+    # are the launches the autotuner keeps for the benchmark.
     prob = wl.cavity(128, 100.0, 0.5)
     p = _oracle_params(oracle, prob)
     r = wl.noise((19, 128, 128, 128), seed=3, amp=0.02)
-    with _lattice(clbm, prob, dtype) as lat:
-        if launch:
+    kw = {"in_place": True} if launch == "in_place" else {}
+    with _lattice(clbm, prob, dtype, **kw) as lat:
+        if launch and launch != "in_place":
             lat.set_launch(*launch)
         rest = lat.get_state()
         lat.set_state(rest * (1 + r))
