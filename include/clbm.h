@@ -11,7 +11,8 @@
  *     cascadedcollision1, with g^_4..g^_18 from Eqs. collisionkernelg4..g18;
  *   - second-order rates omega_4..8 set at every node from the shear rate,
  *     Eq. localvarationsrelaxationtimes with the power law of Eq. 6 and the
- *     strain rate of Eq. strainratetensor; omega_9..18 = 1 (Sec. 3.1);
+ *     strain rate of Eq. strainratetensor; omega_9..18 = 1 as in Sec. 3.1
+ *     unless clbm_set_rates() sets others;
  *   - streaming, Eq. cascadedstreaming1, with halfway bounce-back walls, a
  *     moving lid with a momentum correction and periodic faces (Sec. 4).
  *
@@ -25,7 +26,8 @@
  *     direction order above, holding plain (unshifted) FP64 values f_alpha.
  *   - The caller owns every host and device buffer it passes in.  The library
  *     owns the device memory of a handle (populations, work buffers) and frees
- *     it in clbm_destroy().
+ *     it in clbm_destroy(); it takes that memory from cudaMalloc, or from an
+ *     allocator registered with clbm_set_allocator().
  *   - Work is queued on the handle's CUDA stream.  Calls that return data to
  *     the host synchronise that stream; clbm_step() does not.
  *   - A handle is not thread-safe: use one handle per thread, or serialise.
@@ -148,6 +150,28 @@ int clbm_sync(clbm_handle h);
 /* Free the handle and its device memory.  NULL is accepted. */
 int clbm_destroy(clbm_handle h);
 
+/* ---- External device allocator -------------------------------------------
+ * Not in the paper.  A lattice's long-lived device buffers (populations,
+ * F16R references, check-step velocities and sums) come from cudaMalloc
+ * unless an allocator is registered here, e.g. PyTorch's caching allocator.
+ * Lattices created after the call take their buffers from
+ *   alloc_fn(bytes, device, stream, user) -> device pointer, or NULL when out
+ *     of memory (clbm_create then fails with CLBM_ERR_OOM);
+ * and return them, in clbm_destroy() after synchronising the lattice's
+ * stream, through
+ *   free_fn(ptr, bytes, device, stream, user);
+ * where `stream` is the lattice's CUDA stream and `user` is passed through.
+ * A pointer must be aligned to 256 bytes (the kernels' vector and TMA
+ * accesses assume it): clbm_create returns CLBM_ERR_ARG for a misaligned one,
+ * after handing it back to free_fn.  Each lattice frees through the allocator
+ * it was created with.  NULL for both restores cudaMalloc.  Process-wide: call
+ * it while no clbm_create or clbm_destroy runs.  Scratch buffers of single
+ * calls (field and state transfer, autotuning) stay on the stream-ordered
+ * cudaMallocAsync pool.  Errors: CLBM_ERR_ARG if exactly one function is NULL. */
+typedef void* (*clbm_alloc_fn)(size_t bytes, int device, void* stream, void* user);
+typedef void (*clbm_free_fn)(void* ptr, size_t bytes, int device, void* stream, void* user);
+int clbm_set_allocator(clbm_alloc_fn alloc_fn, clbm_free_fn free_fn, void* user);
+
 /* Pick the launch shape of h's step kernel by timing: thread-block shapes
  * from 32x1 to 256x1 and, for the FP32-math forms, one or two nodes per
  * thread (two nodes are collided together with packed FP32 instructions),
@@ -220,6 +244,10 @@ int clbm_batch_step(clbm_batch b, int64_t nsteps);
  * divergence flag and its step count.  Any pointer may be NULL.  Syncs. */
 int clbm_batch_stats(clbm_batch b, int slot, double* residual, double* mass, int* diverged,
                      int64_t* steps);
+/* The residual and divergence flag of every slot at once (arrays of
+ * `capacity` entries; empty slots give NaN and 0), as clbm_batch_stats.
+ * Either pointer may be NULL.  Syncs once. */
+int clbm_batch_residuals(clbm_batch b, double* residual, int* diverged);
 /* Launch shape: thread block (multiple of 32 threads, <= 256), planes per
  * tile zc >= 1, resident blocks per SM of the persistent grid (negative:
  * the same count with the register-capped kernel variant). */

@@ -39,6 +39,12 @@ class Domain(ctypes.Structure):
 
 _D = ctypes.POINTER(ctypes.c_double)
 _H = ctypes.c_void_p
+# clbm_alloc_fn / clbm_free_fn
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
+                             ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
+                            ctypes.c_void_p)
+_ALLOCATOR = None   # the registered callbacks, kept alive while registered
 
 
 def library_path() -> str:
@@ -77,13 +83,62 @@ def lib():
                                         _D]
             L.clbm_set_launch.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             L.clbm_set_rates.argtypes = [_H, _D]
-            for name in ("clbm_autotune", "clbm_set_launch", "clbm_set_rates",
+            L.clbm_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, ctypes.c_void_p]
+            for name in ("clbm_autotune", "clbm_set_launch", "clbm_set_rates", "clbm_set_allocator",
                          "clbm_create", "clbm_step", "clbm_fields", "clbm_fields_device",
                          "clbm_residual", "clbm_mass", "clbm_get_state", "clbm_set_state",
                          "clbm_steps_done", "clbm_sync", "clbm_destroy", "clbm_collide_nodes"):
                 getattr(L, name).restype = ctypes.c_int
             _LIB = L
     return _LIB
+
+
+def set_allocator(alloc=None, free=None) -> None:
+    """Take the device buffers of lattices created from now on from
+    ``alloc(nbytes, device, stream) -> int`` (a 256-byte aligned device
+    pointer, 0 when out of memory) and return them through
+    ``free(ptr, nbytes, device, stream)`` (``clbm_set_allocator``); ``stream``
+    is the lattice's CUDA stream as an int.  No arguments: back to cudaMalloc.
+    Lattices keep the allocator they were created with."""
+    global _ALLOCATOR
+    L = lib()
+    if alloc is None and free is None:
+        _check(L.clbm_set_allocator(_ALLOC_FN(), _FREE_FN(), None))   # NULL, NULL
+        _RETIRED.append(_ALLOCATOR)
+        _ALLOCATOR = None
+        return
+    if alloc is None or free is None:
+        raise ValueError("give both alloc and free, or neither")
+
+    def _alloc(nbytes, device, stream, user):
+        return int(alloc(int(nbytes), int(device), int(stream or 0)) or 0)
+
+    def _free(ptr, nbytes, device, stream, user):
+        free(int(ptr or 0), int(nbytes), int(device), int(stream or 0))
+
+    cbs = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+    _check(L.clbm_set_allocator(cbs[0], cbs[1], None))
+    # lattices created under an earlier allocator still free through it
+    _RETIRED.append(_ALLOCATOR)
+    _ALLOCATOR = cbs
+
+
+_RETIRED = []
+
+
+def use_torch_allocator() -> None:
+    """Route lattice device memory through PyTorch's caching allocator, so
+    that lattices and tensors share one pool (``torch.cuda.memory_allocated``
+    counts the lattices)."""
+    import torch
+
+    def alloc(nbytes, device, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, device, stream)
+
+    def free(ptr, nbytes, device, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    set_allocator(alloc, free)
 
 
 def _dp(a: np.ndarray | None):
@@ -297,6 +352,7 @@ class Batch:
                                                 ctypes.c_int]
             L.clbm_batch_set_lattice_launch.argtypes = [B, ctypes.c_int, ctypes.c_int,
                                                         ctypes.c_int, ctypes.c_int]
+            L.clbm_batch_residuals.argtypes = [B, _D, ctypes.POINTER(ctypes.c_int)]
             L.clbm_batch_autotune.argtypes = [B, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4 + [_D]
             L.clbm_batch_sync.argtypes = [B]
             L.clbm_batch_destroy.argtypes = [B]
@@ -304,13 +360,14 @@ class Batch:
             L.clbm_batch_last_error.restype = ctypes.c_char_p
             for n in ("clbm_batch_create", "clbm_batch_add", "clbm_batch_remove", "clbm_batch_detach",
                       "clbm_batch_step", "clbm_batch_stats", "clbm_batch_set_launch",
-                      "clbm_batch_set_lattice_launch",
+                      "clbm_batch_set_lattice_launch", "clbm_batch_residuals",
                       "clbm_batch_autotune", "clbm_batch_sync", "clbm_batch_destroy"):
                 getattr(L, n).restype = ctypes.c_int
             L._batch_ready = True
         self._b = ctypes.c_void_p()
         code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
         self.check_interval = int(check_interval)
+        self.capacity = int(capacity)
         self._bcheck(L.clbm_batch_create(code, int(capacity), int(check_interval), stream,
                                          ctypes.byref(self._b)), create=True)
         self.members = {}
@@ -340,6 +397,14 @@ class Batch:
         self._bcheck(lib().clbm_batch_stats(self._b, int(slot), ctypes.byref(R), ctypes.byref(m),
                                             ctypes.byref(dv), ctypes.byref(st)))
         return dict(residual=R.value, mass=m.value, diverged=bool(dv.value), steps=st.value)
+
+    def residuals(self) -> tuple[np.ndarray, np.ndarray]:
+        """Residual and divergence flag of every slot (NaN, False when empty)."""
+        n = self.capacity
+        R = np.empty(n, dtype=np.float64)
+        dv = (ctypes.c_int * n)()
+        self._bcheck(lib().clbm_batch_residuals(self._b, _dp(R), dv))
+        return R, np.array(dv[:], dtype=bool)
 
     def set_launch(self, block_x, block_y, zc, blocks_per_sm) -> None:
         """The persistent kernel with this launch shape."""

@@ -557,6 +557,21 @@ int clbm_batch_stats(clbm_batch b, int slot, double* residual, double* mass, int
   return CLBM_OK;
 }
 
+int clbm_batch_residuals(clbm_batch b, double* residual, int* diverged) {
+  if (!valid(b)) return bfail(b, CLBM_ERR_ARG, "invalid batch");
+  for (int s = 0; s < b->capacity; ++s) {
+    if (b->slots[size_t(s)]) {
+      if (int r = clbm_batch_stats(b, s, residual ? residual + s : nullptr, nullptr,
+                                   diverged ? diverged + s : nullptr, nullptr))
+        return r;
+    } else {
+      if (residual) residual[s] = NAN;
+      if (diverged) diverged[s] = 0;
+    }
+  }
+  return CLBM_OK;
+}
+
 int clbm_batch_set_launch(clbm_batch b, int block_x, int block_y, int zc, int blocks_per_sm) {
   if (!valid(b)) return bfail(b, CLBM_ERR_ARG, "invalid batch");
   const bool cap = blocks_per_sm < 0;

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -36,6 +37,41 @@ int fail(clbm_ctx* h, int code, const std::string& msg) {
 int cuda_fail(clbm_ctx* h, cudaError_t e, const char* what) {
   std::string m = std::string(what) + ": " + cudaGetErrorString(e);
   return fail(h, e == cudaErrorMemoryAllocation ? CLBM_ERR_OOM : CLBM_ERR_CUDA, m);
+}
+
+// The allocator registered with clbm_set_allocator (none: cudaMalloc); a
+// handle copies it at creation.
+std::mutex g_alloc_mu;
+clbm_alloc_fn g_alloc_fn = nullptr;
+clbm_free_fn g_free_fn = nullptr;
+void* g_alloc_user = nullptr;
+
+// A long-lived device buffer of h, from its allocator or cudaMalloc.
+int dev_alloc(clbm_ctx* h, void** p, size_t bytes, const char* what) {
+  *p = nullptr;
+  if (!h->alloc_fn) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      *p = nullptr;
+      return fail(h, CLBM_ERR_OOM, std::string(what) + " allocation failed");
+    }
+    return CLBM_OK;
+  }
+  void* q = h->alloc_fn(bytes, h->device, h->stream, h->alloc_user);
+  if (!q) return fail(h, CLBM_ERR_OOM, std::string(what) + ": the external allocator failed");
+  if (reinterpret_cast<uintptr_t>(q) % 256 != 0) {
+    h->free_fn(q, bytes, h->device, h->stream, h->alloc_user);
+    return fail(h, CLBM_ERR_ARG,
+                std::string(what) + ": the external allocator returned a pointer not aligned "
+                                    "to 256 bytes");
+  }
+  *p = q;
+  return CLBM_OK;
+}
+
+void dev_free(clbm_ctx* h, void* p, size_t bytes) {
+  if (!p) return;
+  if (h->free_fn) h->free_fn(p, bytes, h->device, h->stream, h->alloc_user);
+  else cudaFree(p);
 }
 
 #define CK(h, expr)                                   \
@@ -217,23 +253,32 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
   }
   const size_t pop_bytes = size_t(NQ) * size_t(g.qstride) * h->elem;
   h->in_place = d->in_place != 0;
-  for (int b = 0; b < (h->in_place ? 1 : 2); ++b) {
-    e = cudaMalloc(&h->buf[b], pop_bytes);
-    if (e != cudaSuccess) return cleanup(CLBM_ERR_OOM, "population buffer allocation failed");
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    h->alloc_fn = g_alloc_fn;
+    h->free_fn = g_free_fn;
+    h->alloc_user = g_alloc_user;
   }
+  h->pop_bytes = pop_bytes;
+  h->uprev_bytes = 3 * size_t(g.plane) * g.nz * h->rsize;
+  int rc = CLBM_OK;
+  for (int b = 0; b < (h->in_place ? 1 : 2) && rc == CLBM_OK; ++b)
+    rc = dev_alloc(h, &h->buf[b], pop_bytes, "population buffer");
+  if (rc != CLBM_OK) return cleanup(rc, "clbm_create");
   if (dtype == CLBM_F16R) {
-    const size_t ref_bytes = (size_t(g.plane) * g.nz + 64) * 8;  // 4 halves per node, + slack
-    for (int b = 0; b < 2; ++b) {
-      e = cudaMalloc(&h->ref[b], ref_bytes);
-      if (e == cudaSuccess) e = cudaMemset(h->ref[b], 0, ref_bytes);
-      if (e != cudaSuccess) return cleanup(CLBM_ERR_OOM, "reference buffer allocation failed");
+    h->ref_bytes = (size_t(g.plane) * g.nz + 64) * 8;  // 4 halves per node, + slack
+    for (int b = 0; b < 2 && rc == CLBM_OK; ++b) {
+      rc = dev_alloc(h, &h->ref[b], h->ref_bytes, "reference buffer");
+      if (rc == CLBM_OK && cudaMemsetAsync(h->ref[b], 0, h->ref_bytes, h->stream) != cudaSuccess)
+        rc = fail(h, CLBM_ERR_CUDA, "reference buffer clear failed");
     }
+    if (rc != CLBM_OK) return cleanup(rc, "clbm_create");
   }
-  e = cudaMalloc(&h->uprev, 3 * size_t(g.plane) * g.nz * h->rsize);
-  if (e != cudaSuccess) return cleanup(CLBM_ERR_OOM, "velocity buffer allocation failed");
+  rc = dev_alloc(h, &h->uprev, h->uprev_bytes, "velocity buffer");
+  if (rc != CLBM_OK) return cleanup(rc, "clbm_create");
   // acc: 3 FP64 sums, then the divergence flag and the TMA error word
-  e = cudaMalloc(&h->acc, 4 * sizeof(double));
-  if (e != cudaSuccess) return cleanup(CLBM_ERR_OOM, "reduction buffer allocation failed");
+  rc = dev_alloc(h, reinterpret_cast<void**>(&h->acc), 4 * sizeof(double), "reduction buffer");
+  if (rc != CLBM_OK) return cleanup(rc, "clbm_create");
   h->flag = reinterpret_cast<int*>(h->acc + 3);
   e = cudaMallocHost(&h->host, 4 * sizeof(double));
   if (e != cudaSuccess) return cleanup(CLBM_ERR_OOM, "pinned buffer allocation failed");
@@ -605,15 +650,25 @@ int clbm_destroy(clbm_handle h) {
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (int b = 0; b < 2; ++b) {
-    if (h->buf[b]) cudaFree(h->buf[b]);
-    if (h->ref[b]) cudaFree(h->ref[b]);
+    dev_free(h, h->buf[b], h->pop_bytes);
+    dev_free(h, h->ref[b], h->ref_bytes);
   }
-  if (h->uprev) cudaFree(h->uprev);
-  if (h->acc) cudaFree(h->acc);
+  dev_free(h, h->uprev, h->uprev_bytes);
+  dev_free(h, h->acc, 4 * sizeof(double));
   if (h->host) cudaFreeHost(h->host);
   if (h->check_done) cudaEventDestroy(h->check_done);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
+  return CLBM_OK;
+}
+
+int clbm_set_allocator(clbm_alloc_fn alloc_fn, clbm_free_fn free_fn, void* user) {
+  if ((alloc_fn == nullptr) != (free_fn == nullptr))
+    return fail(nullptr, CLBM_ERR_ARG, "give both allocator functions, or neither");
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc_fn = alloc_fn;
+  g_free_fn = free_fn;
+  g_alloc_user = alloc_fn ? user : nullptr;
   return CLBM_OK;
 }
 

@@ -36,6 +36,10 @@ struct clbm_ctx {
   int npt = 1;           // nodes per thread (1 or 2), + 4 for the register-capped kernel,
                          // or TMA_NPT + 32 v for the TMA-staged kernel of shape v
   struct clbm_batch_ctx* batch = nullptr;  // batch stepping this lattice, if any
+  clbm_alloc_fn alloc_fn = nullptr;  // registered allocator at creation (NULL: cudaMalloc)
+  clbm_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
+  size_t pop_bytes = 0, ref_bytes = 0, uprev_bytes = 0;  // sizes handed to free_fn
   std::string err;
 };
 

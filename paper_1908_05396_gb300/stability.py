@@ -74,8 +74,9 @@ def batch_runner(L: int = 64, steps: int = 50_000, dtype: str = "f32",
                     k = min(chunk, steps - done)
                     b.step(k)
                     done += k
+                    _, diverged = b.residuals()
                     for s, i in list(slots.items()):
-                        if b.stats(s)["diverged"]:
+                        if diverged[s]:
                             stable[i] = False
                             b.remove(s).close()
                             del slots[s]

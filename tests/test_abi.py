@@ -82,3 +82,15 @@ def test_null_handle_calls_fail_cleanly(clbm):
     assert L.clbm_step(None, 1) == clbm.ERR_ARG
     assert L.clbm_residual(None, ctypes.byref(out)) == clbm.ERR_ARG
     assert L.clbm_destroy(None) == clbm.OK
+
+
+def test_set_allocator_needs_both_functions(clbm):
+    L = clbm.lib()
+    alloc = clbm._ALLOC_FN(lambda n, d, s, u: 0)
+    free = clbm._FREE_FN(lambda p, n, d, s, u: None)
+    null_a, null_f = clbm._ALLOC_FN(), clbm._FREE_FN()
+    assert L.clbm_set_allocator(alloc, null_f, None) == clbm.ERR_ARG
+    assert L.clbm_set_allocator(null_a, free, None) == clbm.ERR_ARG
+    assert L.clbm_set_allocator(null_a, null_f, None) == clbm.OK
+    with pytest.raises(ValueError):
+        clbm.set_allocator(lambda n, d, s: 0, None)

@@ -77,8 +77,11 @@ def test_batch_equals_alone(clbm, dtype, mode):
         _set_mode(b, mode)
         slots = [b.add(lt) for lt in lats]
         b.step(steps)
+        R_all, dv_all = b.residuals()
+        assert np.isnan(R_all[len(lats):]).all() and not dv_all.any()
         for s, lt, (f_ref, R_ref, m_ref) in zip(slots, lats, alone):
             st = b.stats(s)
+            assert st["residual"] == R_all[s]
             assert st["steps"] == steps and not st["diverged"]
             f = lt.get_state()
             _same(f, f_ref, dtype)
