@@ -184,9 +184,40 @@ def _cpu_baseline(budget_s: float = 12.0):
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": nodes / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"{steps} oracle step(s) of the three 128^3 Re=100 cavities "
-                      f"(n=0.5,1,1.5), FP64, OpenMP over z-planes, {dt:.1f} s"}
+    out = {"value": nodes / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+           "sample": f"{steps} oracle step(s) of the three 128^3 Re=100 cavities "
+                     f"(n=0.5,1,1.5), FP64, OpenMP over z-planes, {dt:.1f} s"}
+    # the same oracle on one core, in a fresh process (its thread count is
+    # fixed when the OpenMP runtime starts)
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-one-core"],
+                           env=dict(os.environ, OMP_NUM_THREADS="1"), capture_output=True,
+                           text=True, timeout=120)
+        out["single_core"] = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, not fatal: the multi-core number stands
+        out["single_core"] = {"error": str(e)[:200]}
+    return out
+
+
+def run_oracle_one_core():
+    """The oracle on one core: steps of a 64^3 cavity (Re 100, n 0.5) for
+    about 5 s."""
+    import oracle
+    from paper_1908_05396_gb300 import workloads as wl
+    oracle.build()
+    prob = wl.cavity(64, RE_BENCH, 0.5)
+    p = oracle.Params(nx=prob.nx, ny=prob.ny, nz=prob.nz, face=prob.face, K=prob.K, n=prob.n,
+                      U=prob.U_lid)
+    f = oracle.run(p, oracle.rest_state(p), 1)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < 5.0:
+        f = oracle.run(p, f, 1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    print(json.dumps({"value": prob.N * steps / dt / 1e6, "unit": "MLUPS", "cores": 1,
+                      "sample": f"{steps} oracle steps of a 64^3 cavity (Re 100, n 0.5), FP64, "
+                                f"OMP_NUM_THREADS=1, {dt:.1f} s"}))
+    return 0
 
 
 REF_SLAB = 8   # z-planes of each cavity per reference step (same per-node work)
@@ -402,6 +433,21 @@ def run_ours(args):
     return 0
 
 
+def _clamp_active_nodes(lats, probs, nu_min=5e-4, nu_max=10.0) -> dict:
+    """Nodes whose viscosity sits on a clamp after the timed steps: the
+    reported shear rate is the one at the clamped omega, and the power law
+    evaluated there lies beyond the clamp exactly when the clamp binds."""
+    import numpy as np
+    lo = hi = 0
+    for lt, p in zip(lats, probs):
+        rho, _, gd = lt.fields()
+        with np.errstate(divide="ignore", over="ignore", invalid="ignore"):
+            nu = p.K / rho * np.power(gd, p.n - 1.0)
+        lo += int(np.count_nonzero(nu < nu_min * (1 - 1e-4)))
+        hi += int(np.count_nonzero(nu > nu_max * (1 + 1e-4)))
+    return {"at_nu_min": lo, "at_nu_max": hi}
+
+
 def _batch_bench(clbm, torch, wl, steps, peak):
     """64 seeded cavities of uneven size in one batch (FP32), against the same
     lattices stepped one launch at a time."""
@@ -421,7 +467,8 @@ def _batch_bench(clbm, torch, wl, steps, peak):
             b.add(lt)
         tuned = b.autotune(4)
         dt = timed(b)
-        diverged = sum(1 for s in range(len(lats)) if b.stats(s)["diverged"])
+        diverged = int(b.residuals()[1].sum())
+        clamped = _clamp_active_nodes(lats, probs)
         # both modes at their usual best shapes, whichever the tuner kept
         b.set_launch(32, 4, 2, -8)
         dt_persistent = timed(b)
@@ -442,10 +489,22 @@ def _batch_bench(clbm, torch, wl, steps, peak):
     dt_alone = time.perf_counter() - t0
     for lt in lats:
         lt.close()
+    # one cavity of about the same node count, for the batch's efficiency
+    L1 = round(N ** (1.0 / 3.0))
+    with clbm.Lattice(**wl.cavity(L1, 100.0, 1.0).kwargs(), dtype="f32") as one:
+        one.autotune(5)
+        one.step(50)
+        one.sync()
+        t0 = time.perf_counter()
+        one.step(steps)
+        one.sync()
+        dt_one = time.perf_counter() - t0
     gbs = 152 * N * steps / dt / 1e9
     return {"workload": "64 cavities, L~U{32..96}, Re~U[50,500], n~U[0.4,1.6], U=0.05, FP32, seed 0",
             "nodes": N, "steps": steps, "MLUPS": mlups, "GB/s": gbs, "frac_of_hbm": gbs / peak,
-            "launch": tuned, "diverged_lattices": diverged,
+            "launch": tuned, "diverged_lattices": diverged, "clamp_active_nodes": clamped,
+            "equal_size_single_MLUPS": L1 ** 3 * steps / dt_one / 1e6,
+            "equal_size_single": f"one {L1}^3 cavity (Re 100, n 1), FP32, autotuned",
             "persistent_MLUPS": N * steps / dt_persistent / 1e6,
             "persistent_launch": "one persistent launch per step: 32x4 tiles, zc 2, 8 capped CTAs/SM",
             "per_lattice_MLUPS": N * steps / dt_per_lattice / 1e6,
@@ -802,7 +861,10 @@ def main():
     ap.add_argument("--stability-dtype", default="f32", choices=["f64", "f32"])
     ap.add_argument("--stability-confirm", action="store_true",
                     help="re-run the unit-rate brackets at tau_p = 0.51 in FP64")
+    ap.add_argument("--oracle-one-core", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_one_core:
+        return run_oracle_one_core()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -54,11 +54,20 @@ def test_channel_configuration_matches_power_law_profile(clbm, dtype):
     prob = wl.Problem("channel", 4, H, 4, (P, P, W_, W_, P, P), K=K, n=n, body_force=(G, 0.0, 0.0))
     with clbm.Lattice(**prob.kwargs(), dtype=dtype, check_interval=100) as lat:
         _steady(lat, 1e-10 if dtype == "f64" else 1e-8, 20000, 2_000_000)
-        _, u, _ = lat.fields()
+        _, u, gd = lat.fields()
     _, ua = _analytic_channel(H, n, G, K)
     un = u[0].mean(axis=(0, 2))
     assert abs(ua.max() - 0.02) < 1e-6      # centreline between the two middle nodes
     assert np.linalg.norm(un - ua) / np.linalg.norm(ua) < 1e-2
+    # the shear-rate output (Eq. strainratetensor, from the non-equilibrium
+    # moments) against the analytic |du/dy| = (G |y| / K)^(1/n), away from
+    # the centreline, where it vanishes, and from the wall nodes
+    y = np.arange(H) + 0.5 - H / 2
+    gd_a = (G * np.abs(y) / K) ** (1.0 / n)
+    sel = (np.abs(y) > H / 8) & (np.abs(y) < H / 2 - 2)
+    gdn = gd.mean(axis=(0, 2))
+    err = np.abs(gdn[sel] - gd_a[sel]) / gd_a[sel]
+    assert err.max() <= (1e-5 if dtype == "f64" else 1e-3)   # measured 2.5e-6 / 2.1e-4
     # the profile is the same in every x column and z plane
     assert np.abs(u[0] - un[None, :, None]).max() <= (1e-9 if dtype == "f64" else 1e-5) * ua.max()
 
