@@ -52,7 +52,7 @@ extern "C" {
 #define CLBM_ERR_CUDA -3        /* CUDA runtime error */
 #define CLBM_ERR_DIVERGED -4    /* NaN/Inf or density outside [0.5, 2] seen */
 #define CLBM_ERR_TIMEOUT -5     /* a bounded device wait gave up */
-#define CLBM_ERR_UNSUPPORTED -6 /* valid request this build does not support */
+#define CLBM_ERR_UNSUPPORTED -6 /* valid request the library does not support */
 
 /* Storage precision of the populations.
  *   CLBM_F64  : f - w rho0 stored in FP64, collision in FP64.
