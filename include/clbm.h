@@ -89,8 +89,10 @@ typedef struct {
   void* stream;        /* cudaStream_t to queue on; NULL -> library-owned */
   int in_place;        /* 1: one population buffer, streamed in place (not in
                         * the paper): half the memory, the same results and
-                        * bytes per update; FP64, FP32 and F16S only, not in
-                        * batches (the server's lattices ignore it) */
+                        * bytes per update; FP64, FP32 and F16S only; in a
+                        * batch only with one launch per lattice
+                        * (clbm_batch_set_lattice_launch); the server's
+                        * lattices ignore it) */
 } clbm_domain;
 
 typedef struct clbm_ctx* clbm_handle;
@@ -230,7 +232,9 @@ typedef struct clbm_batch_ctx* clbm_batch;
 int clbm_batch_create(clbm_dtype dtype, int capacity, int check_interval, void* stream,
                       clbm_batch* out);
 /* Attach h (same dtype and device, not in another batch, 19 x padded nodes
- * < 2^31); its queued work is waited for; *slot receives its slot. */
+ * < 2^31; an in-place lattice only in the one-launch-per-lattice mode, else
+ * CLBM_ERR_UNSUPPORTED); its queued work is waited for; *slot receives its
+ * slot. */
 int clbm_batch_add(clbm_batch b, clbm_handle h, int* slot);
 /* Detach the lattice in `slot` (waits for the batch's queued work). */
 int clbm_batch_remove(clbm_batch b, int slot);
@@ -248,9 +252,11 @@ int clbm_batch_stats(clbm_batch b, int slot, double* residual, double* mass, int
  * `capacity` entries; empty slots give NaN and 0), as clbm_batch_stats.
  * Either pointer may be NULL.  Syncs once. */
 int clbm_batch_residuals(clbm_batch b, double* residual, int* diverged);
-/* Launch shape: thread block (multiple of 32 threads, <= 256), planes per
- * tile zc >= 1, resident blocks per SM of the persistent grid (negative:
- * the same count with the register-capped kernel variant). */
+/* The persistent kernel with this launch shape: thread block (multiple of
+ * 32 threads, <= 256), planes per tile zc >= 1, resident blocks per SM of
+ * the persistent grid (negative: the same count with the register-capped
+ * kernel variant).  CLBM_ERR_UNSUPPORTED while an in-place lattice is
+ * attached. */
 int clbm_batch_set_launch(clbm_batch b, int block_x, int block_y, int zc, int blocks_per_sm);
 /* One launch per lattice instead of the persistent kernel (FP64, FP32,
  * F16S; CLBM_ERR_UNSUPPORTED for F16R, whose rounding is seeded by the batch's
@@ -260,13 +266,14 @@ int clbm_batch_set_launch(clbm_batch b, int block_x, int block_y, int zc, int bl
  * (1..16) streams, largest first onto the least-loaded one.  The streams fork
  * from the batch's stream and join it around each check interval, which is
  * still one CUDA graph; a change of membership recaptures it.  Results are
- * those of clbm_step on each lattice.  clbm_batch_set_launch() returns to the
- * persistent kernel. */
+ * those of clbm_step on each lattice.  This mode also steps in-place
+ * lattices.  clbm_batch_set_launch() returns to the persistent kernel. */
 int clbm_batch_set_lattice_launch(clbm_batch b, int block_x, int block_y, int npt, int streams);
 /* Time block shapes x zc x blocks-per-SM x register cap of the persistent
  * kernel and, except for F16R, block shapes x kernel variant x streams of one
  * launch per lattice, on the attached lattices (states saved and restored),
- * and keep the fastest.  Persistent kernel: *blocks_per_sm is negative when
+ * and keep the fastest (only the latter while an in-place lattice is
+ * attached).  Persistent kernel: *blocks_per_sm is negative when
  * the capped variant won.  One launch per lattice: *zc is 0, *block_x and
  * *block_y are the lattices' block, |*blocks_per_sm| is the stream count,
  * negative for the register-capped kernel. */

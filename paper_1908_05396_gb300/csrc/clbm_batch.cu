@@ -249,11 +249,27 @@ cudaError_t launch_lattices(clbm_batch_ctx* b, bool check, int flip) {
     if (!h) continue;
     double* acc = b->d_acc + 4 * size_t(s);
     CheckBufs cb{h->uprev, acc, reinterpret_cast<int*>(acc + 3)};
+    const cudaStream_t st = pl_stream(b, b->stream_of[size_t(s)]);
+    cudaError_t e;
+    if (h->in_place) {  // one buffer, the layout alternating with the steps
+      const int lay = h->layout ^ flip;
+      switch (b->dtype) {
+        case CLBM_F64:
+          e = launch_step_aa_f64(h->buf[0], h->g, h->P, cb, check, b->pl_block, b->pl_npt, lay, st);
+          break;
+        case CLBM_F32:
+          e = launch_step_aa_f32(h->buf[0], h->g, h->P, cb, check, b->pl_block, b->pl_npt, lay, st);
+          break;
+        default:
+          e = launch_step_aa_f16(h->buf[0], h->g, h->P, cb, check, b->pl_block, b->pl_npt, lay, st);
+          break;
+      }
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     const int c = h->cur ^ flip;
     const void* src = h->buf[c];
     void* dst = h->buf[1 - c];
-    const cudaStream_t st = pl_stream(b, b->stream_of[size_t(s)]);
-    cudaError_t e;
     switch (b->dtype) {
       case CLBM_F64:
         e = launch_step_f64(src, dst, h->g, h->P, cb, check, b->pl_block, b->pl_npt, st);
@@ -281,7 +297,8 @@ int upload(clbm_batch_ctx* b) {
   for (int pass = 0; pass < 2; ++pass) {
     for (int s = 0; s < b->capacity; ++s) {
       clbm_ctx* h = b->slots[s];
-      if (!h || (h->P.has_force != 0) != (pass == 1)) continue;
+      // in-place lattices (mode 1 only) have no place in the tile tables
+      if (!h || h->in_place || (h->P.has_force != 0) != (pass == 1)) continue;
       const int tx = (h->g.nx + int(b->block.x) - 1) / int(b->block.x);
       const int ty = (h->g.ny + int(b->block.y) - 1) / int(b->block.y);
       const int tz = (h->g.nz + b->zc - 1) / b->zc;   // chunks of zc planes
@@ -336,7 +353,10 @@ void advance(clbm_batch_ctx* b, int64_t n) {
   for (clbm_ctx* h : b->slots)
     if (h) {
       h->steps += n;
-      if (n & 1) h->cur = 1 - h->cur;
+      if (n & 1) {
+        if (h->in_place) h->layout ^= 1;
+        else h->cur = 1 - h->cur;
+      }
     }
   b->steps += n;
 }
@@ -477,8 +497,10 @@ int clbm_batch_create(clbm_dtype dtype, int capacity, int check_interval, void* 
 int clbm_batch_add(clbm_batch b, clbm_handle h, int* slot) {
   if (!valid(b) || !h || !h->buf[0]) return bfail(b, CLBM_ERR_ARG, "invalid batch or handle");
   if (h->dtype != b->dtype) return bfail(b, CLBM_ERR_ARG, "lattice dtype differs from the batch's");
-  if (h->in_place)
-    return bfail(b, CLBM_ERR_UNSUPPORTED, "in-place lattices are not batched (two-buffer tiles)");
+  if (h->in_place && b->mode != 1)
+    return bfail(b, CLBM_ERR_UNSUPPORTED,
+                 "in-place lattices join a batch only in its one-launch-per-lattice mode "
+                 "(clbm_batch_set_lattice_launch): the persistent kernel's tiles need two buffers");
   if (h->device != b->device) return bfail(b, CLBM_ERR_ARG, "lattice lives on another device");
   if (h->batch) return bfail(b, CLBM_ERR_ARG, "lattice is already in a batch");
   if (int64_t(NQ) * h->g.qstride >= (int64_t(1) << 31))
@@ -579,6 +601,10 @@ int clbm_batch_set_launch(clbm_batch b, int block_x, int block_y, int zc, int bl
   if (block_x < 1 || block_y < 1 || block_x * block_y > 256 || (block_x * block_y) % 32 ||
       zc < 1 || blocks_per_sm < 1 || blocks_per_sm > 32)
     return bfail(b, CLBM_ERR_ARG, "bad launch shape");
+  for (clbm_ctx* h : b->slots)
+    if (h && h->in_place)
+      return bfail(b, CLBM_ERR_UNSUPPORTED,
+                   "the batch holds in-place lattices: the persistent kernel needs two buffers");
   BCK(b, cudaSetDevice(b->device));
   BCK(b, cudaStreamSynchronize(b->stream));
   b->block = dim3(block_x, block_y, 1);
@@ -619,8 +645,9 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
   // Save every lattice's current state: tuning runs real steps.
   BCK(b, cudaStreamSynchronize(b->stream));
   std::vector<void*> saved(size_t(b->capacity), nullptr);
-  std::vector<int> cur0(size_t(b->capacity), 0);
+  std::vector<int> cur0(size_t(b->capacity), 0), lay0(size_t(b->capacity), 0);
   std::vector<int64_t> steps0(size_t(b->capacity), 0);
+  bool any_in_place = false;
   cudaError_t err = cudaSuccess;
   for (int s = 0; s < b->capacity && err == cudaSuccess; ++s) {
     clbm_ctx* h = b->slots[s];
@@ -634,7 +661,9 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
       err = cudaMemcpyAsync(static_cast<char*>(saved[s]) + bytes, h->ref[h->cur], rbytes,
                             cudaMemcpyDeviceToDevice, b->stream);
     cur0[s] = h->cur;
+    lay0[s] = h->layout;
     steps0[s] = h->steps;
+    any_in_place = any_in_place || h->in_place;
   }
   const int64_t bsteps0 = b->steps;
   const dim3 block0 = b->block;
@@ -649,7 +678,8 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (err == cudaSuccess) err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
-  for (int capped = 0; capped <= 1; ++capped)
+  // the persistent kernel only when every lattice has two buffers
+  for (int capped = 0; capped <= 1 && !any_in_place; ++capped)
   for (auto& sh : shapes)
     for (int z : zcs)
       for (int bp : bpss) {
@@ -735,6 +765,7 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
     clbm_ctx* h = b->slots[s];
     if (!h || !saved[s]) continue;
     h->cur = cur0[s];
+    h->layout = lay0[s];
     h->steps = steps0[s];
     const size_t bytes = size_t(NQ) * size_t(h->g.qstride) * h->elem;
     const size_t rbytes = h->ref[0] ? (size_t(h->g.plane) * h->g.nz + 64) * 8 : 0;

@@ -110,3 +110,46 @@ def test_in_place_limits(clbm):
         with clbm.Batch("f32", capacity=2) as batch:
             with pytest.raises(clbm.CLBMError):
                 batch.add(b)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s"])
+def test_in_place_lattices_in_a_lattice_launch_batch(clbm, dtype):
+    # In-place lattices join a batch in its one-launch-per-lattice mode,
+    # beside a two-buffer lattice; with the same kernel each one matches the
+    # same lattice stepped alone bit for bit, over graph intervals and an odd
+    # tail of single steps.
+    probs = [_MIXED, _PERX, _BOX]
+    alone = []
+    for p in probs + [_MIXED]:
+        with clbm.Lattice(**p.kwargs(), dtype=dtype, check_interval=50,
+                          in_place=len(alone) < 3) as a:
+            a.set_launch(32, 2, 5)
+            a.step(157)
+            alone.append(a.get_state())
+    lats = [clbm.Lattice(**p.kwargs(), dtype=dtype, check_interval=50, in_place=True)
+            for p in probs]
+    lats.append(clbm.Lattice(**_MIXED.kwargs(), dtype=dtype, check_interval=50))
+    with clbm.Batch(dtype, capacity=4, check_interval=50) as b:
+        with pytest.raises(clbm.CLBMError):
+            b.add(lats[0])                      # the persistent kernel needs two buffers
+        b.set_lattice_launch(32, 2, 5, 2)
+        for lt in lats:
+            b.add(lt)
+        with pytest.raises(clbm.CLBMError):
+            b.set_launch(32, 4, 1, 4)
+        b.step(157)
+        for lt, f in zip(lats, alone):
+            assert lt.steps_done() == 157
+            assert np.array_equal(lt.get_state(), f)
+        f0 = [lt.get_state() for lt in lats]
+        info = b.autotune(3)
+        assert info["mode"] == "per_lattice"
+        for lt, f in zip(lats, f0):
+            assert np.array_equal(lt.get_state(), f) and lt.steps_done() == 157
+        b.apply_launch(info)
+        b.step(43)
+    for lt, p in zip(lats, probs + [_MIXED]):
+        with clbm.Lattice(**p.kwargs(), dtype=dtype, check_interval=50) as ref:
+            ref.step(200)
+            _same(lt.get_state(), ref.get_state(), dtype)
+        lt.close()
