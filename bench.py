@@ -467,7 +467,7 @@ def _batch_bench(clbm, torch, wl, steps, peak):
             b.add(lt)
         tuned = b.autotune(4)
         dt = timed(b)
-        diverged = int(b.residuals()[1].sum())
+        diverged = int(b.stats_all()["diverged"].sum())
         clamped = _clamp_active_nodes(lats, probs)
         # both modes at their usual best shapes, whichever the tuner kept
         b.set_launch(32, 4, 2, -8)

@@ -248,10 +248,10 @@ int clbm_batch_step(clbm_batch b, int64_t nsteps);
  * divergence flag and its step count.  Any pointer may be NULL.  Syncs. */
 int clbm_batch_stats(clbm_batch b, int slot, double* residual, double* mass, int* diverged,
                      int64_t* steps);
-/* The residual and divergence flag of every slot at once (arrays of
- * `capacity` entries; empty slots give NaN and 0), as clbm_batch_stats.
- * Either pointer may be NULL.  Syncs once. */
-int clbm_batch_residuals(clbm_batch b, double* residual, int* diverged);
+/* clbm_batch_stats of every slot at once: arrays of `capacity` entries
+ * (empty slots give NaN, NaN, 0, -1).  Any pointer may be NULL.  Syncs once. */
+int clbm_batch_stats_all(clbm_batch b, double* residual, double* mass, int* diverged,
+                         int64_t* steps);
 /* The persistent kernel with this launch shape: thread block (multiple of
  * 32 threads, <= 256), planes per tile zc >= 1, resident blocks per SM of
  * the persistent grid (negative: the same count with the register-capped

@@ -352,7 +352,8 @@ class Batch:
                                                 ctypes.c_int]
             L.clbm_batch_set_lattice_launch.argtypes = [B, ctypes.c_int, ctypes.c_int,
                                                         ctypes.c_int, ctypes.c_int]
-            L.clbm_batch_residuals.argtypes = [B, _D, ctypes.POINTER(ctypes.c_int)]
+            L.clbm_batch_stats_all.argtypes = [B, _D, _D, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_int64)]
             L.clbm_batch_autotune.argtypes = [B, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 4 + [_D]
             L.clbm_batch_sync.argtypes = [B]
             L.clbm_batch_destroy.argtypes = [B]
@@ -360,7 +361,7 @@ class Batch:
             L.clbm_batch_last_error.restype = ctypes.c_char_p
             for n in ("clbm_batch_create", "clbm_batch_add", "clbm_batch_remove", "clbm_batch_detach",
                       "clbm_batch_step", "clbm_batch_stats", "clbm_batch_set_launch",
-                      "clbm_batch_set_lattice_launch", "clbm_batch_residuals",
+                      "clbm_batch_set_lattice_launch", "clbm_batch_stats_all",
                       "clbm_batch_autotune", "clbm_batch_sync", "clbm_batch_destroy"):
                 getattr(L, n).restype = ctypes.c_int
             L._batch_ready = True
@@ -398,13 +399,17 @@ class Batch:
                                             ctypes.byref(dv), ctypes.byref(st)))
         return dict(residual=R.value, mass=m.value, diverged=bool(dv.value), steps=st.value)
 
-    def residuals(self) -> tuple[np.ndarray, np.ndarray]:
-        """Residual and divergence flag of every slot (NaN, False when empty)."""
+    def stats_all(self) -> dict:
+        """``stats`` of every slot as arrays of ``capacity`` entries (empty
+        slots: residual and mass NaN, diverged False, steps -1); one sync."""
         n = self.capacity
         R = np.empty(n, dtype=np.float64)
+        m = np.empty(n, dtype=np.float64)
         dv = (ctypes.c_int * n)()
-        self._bcheck(lib().clbm_batch_residuals(self._b, _dp(R), dv))
-        return R, np.array(dv[:], dtype=bool)
+        st = (ctypes.c_int64 * n)()
+        self._bcheck(lib().clbm_batch_stats_all(self._b, _dp(R), _dp(m), dv, st))
+        return dict(residual=R, mass=m, diverged=np.array(dv[:], dtype=bool),
+                    steps=np.array(st[:], dtype=np.int64))
 
     def set_launch(self, block_x, block_y, zc, blocks_per_sm) -> None:
         """The persistent kernel with this launch shape."""

@@ -430,6 +430,26 @@ int capture(clbm_batch_ctx* b) {
 
 bool valid(const clbm_batch_ctx* b) { return b && b->d_desc; }
 
+// Results of the last completed check of an occupied slot (the stream has
+// been synchronised): residual as clbm_residual (+Inf before two checks in
+// this batch), mass, divergence flag, steps.
+void slot_stats(const clbm_batch_ctx* b, int slot, double* residual, double* mass,
+                int* diverged, int64_t* steps) {
+  const double* a = b->h_acc + 4 * slot;
+  const clbm_ctx* h = b->slots[size_t(slot)];
+  if (residual) {
+    if (b->slot_checks[size_t(slot)] < 2) *residual = INFINITY;
+    else if (!(a[1] > 0.0)) *residual = a[0] == 0.0 ? 0.0 : INFINITY;
+    else *residual = std::sqrt(a[0]) / (double(b->check_interval) * std::sqrt(a[1]));
+  }
+  if (mass) *mass = double(h->g.nx) * h->g.ny * h->g.nz * h->g.rho0 + a[2];
+  int f = 0;
+  std::memcpy(&f, &a[3], sizeof(int));
+  if (b->slot_checks[size_t(slot)] < 1) f = 0;
+  if (diverged) *diverged = f;
+  if (steps) *steps = h->steps;
+}
+
 // The kernel skips any tile whose descriptor fails its checks and sets the
 // header's error word; report that instead of silently wrong results.
 int check_tables(clbm_batch_ctx* b) {
@@ -563,32 +583,25 @@ int clbm_batch_stats(clbm_batch b, int slot, double* residual, double* mass, int
   BCK(b, cudaSetDevice(b->device));
   BCK(b, cudaStreamSynchronize(b->stream));
   if (int r = check_tables(b)) return r;
-  const double* a = b->h_acc + 4 * slot;
-  clbm_ctx* h = b->slots[slot];
-  if (residual) {
-    if (b->slot_checks[slot] < 2) *residual = INFINITY;
-    else if (!(a[1] > 0.0)) *residual = a[0] == 0.0 ? 0.0 : INFINITY;
-    else *residual = std::sqrt(a[0]) / (double(b->check_interval) * std::sqrt(a[1]));
-  }
-  if (mass) *mass = double(h->g.nx) * h->g.ny * h->g.nz * h->g.rho0 + a[2];
-  int f = 0;
-  std::memcpy(&f, &a[3], sizeof(int));
-  if (b->slot_checks[slot] < 1) f = 0;
-  if (diverged) *diverged = f;
-  if (steps) *steps = h->steps;
+  slot_stats(b, slot, residual, mass, diverged, steps);
   return CLBM_OK;
 }
 
-int clbm_batch_residuals(clbm_batch b, double* residual, int* diverged) {
+int clbm_batch_stats_all(clbm_batch b, double* residual, double* mass, int* diverged,
+                         int64_t* steps) {
   if (!valid(b)) return bfail(b, CLBM_ERR_ARG, "invalid batch");
+  BCK(b, cudaSetDevice(b->device));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  if (int r = check_tables(b)) return r;
   for (int s = 0; s < b->capacity; ++s) {
     if (b->slots[size_t(s)]) {
-      if (int r = clbm_batch_stats(b, s, residual ? residual + s : nullptr, nullptr,
-                                   diverged ? diverged + s : nullptr, nullptr))
-        return r;
+      slot_stats(b, s, residual ? residual + s : nullptr, mass ? mass + s : nullptr,
+                 diverged ? diverged + s : nullptr, steps ? steps + s : nullptr);
     } else {
       if (residual) residual[s] = NAN;
+      if (mass) mass[s] = NAN;
       if (diverged) diverged[s] = 0;
+      if (steps) steps[s] = -1;
     }
   }
   return CLBM_OK;

@@ -77,6 +77,10 @@ struct clbm_server_ctx {
   int64_t next_id = 1;
   int64_t lups = 0;                 // lattice-node updates done
   double busy = 0;                  // seconds with at least one lattice active
+  // per-slot check results of the batch (max_active entries)
+  std::vector<double> st_R, st_mass;
+  std::vector<int> st_div;
+  std::vector<int64_t> st_steps;
   std::string err;
 };
 
@@ -203,16 +207,18 @@ void worker_loop(clbm_server_ctx* s) {
       break;
     }
     s->lups += nodes * s->check_interval;
-    // 3. retirement
+    // 3. retirement, from every slot's check results (one synchronisation)
+    const bool stats_ok = clbm_batch_stats_all(s->batch, s->st_R.data(), s->st_mass.data(),
+                                               s->st_div.data(), s->st_steps.data()) == CLBM_OK;
     std::vector<Active> keep;
     for (Active& a : s->active) {
-      double R = INFINITY, mass = 0;
-      int div = 0;
-      int64_t steps = 0;
-      if (clbm_batch_stats(s->batch, a.slot, &R, &mass, &div, &steps) != CLBM_OK) {
-        finish(s, a, CLBM_SOLVE_ERROR, INFINITY, 0.0, steps);
+      if (!stats_ok) {
+        finish(s, a, CLBM_SOLVE_ERROR, INFINITY, 0.0, 0);
         continue;
       }
+      const double R = s->st_R[size_t(a.slot)], mass = s->st_mass[size_t(a.slot)];
+      const int div = s->st_div[size_t(a.slot)];
+      const int64_t steps = s->st_steps[size_t(a.slot)];
       if (div) {
         finish(s, a, CLBM_SOLVE_DIVERGED, R, mass, steps);
       } else if (R <= a.req.tol) {
@@ -269,6 +275,10 @@ int clbm_server_create(clbm_dtype dtype, double hbm_budget_bytes, int max_active
   s->dtype = dtype;
   s->budget = hbm_budget_bytes;
   s->max_active = max_active;
+  s->st_R.assign(size_t(max_active), 0.0);
+  s->st_mass.assign(size_t(max_active), 0.0);
+  s->st_div.assign(size_t(max_active), 0);
+  s->st_steps.assign(size_t(max_active), 0);
   s->check_interval = check_interval;
   s->t0 = Clock::now();
   cudaGetDevice(&s->device);

@@ -74,7 +74,7 @@ def batch_runner(L: int = 64, steps: int = 50_000, dtype: str = "f32",
                     k = min(chunk, steps - done)
                     b.step(k)
                     done += k
-                    _, diverged = b.residuals()
+                    diverged = b.stats_all()["diverged"]
                     for s, i in list(slots.items()):
                         if diverged[s]:
                             stable[i] = False

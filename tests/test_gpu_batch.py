@@ -77,11 +77,13 @@ def test_batch_equals_alone(clbm, dtype, mode):
         _set_mode(b, mode)
         slots = [b.add(lt) for lt in lats]
         b.step(steps)
-        R_all, dv_all = b.residuals()
-        assert np.isnan(R_all[len(lats):]).all() and not dv_all.any()
+        al = b.stats_all()
+        assert np.isnan(al["residual"][len(lats):]).all() and not al["diverged"].any()
+        assert (al["steps"][len(lats):] == -1).all()
         for s, lt, (f_ref, R_ref, m_ref) in zip(slots, lats, alone):
             st = b.stats(s)
-            assert st["residual"] == R_all[s]
+            assert st["residual"] == al["residual"][s] and st["mass"] == al["mass"][s]
+            assert st["steps"] == al["steps"][s]
             assert st["steps"] == steps and not st["diverged"]
             f = lt.get_state()
             _same(f, f_ref, dtype)
