@@ -55,6 +55,8 @@ def _same(f, f_ref, dtype):
 def _set_mode(b, mode):
     if mode == "per_lattice":
         b.set_lattice_launch(32, 2, 5, 3)
+    else:
+        b.set_launch(32, 4, 1, 4)       # uncapped: the arithmetic of the lone default kernel
 
 
 @pytest.mark.parametrize("mode", ["persistent", "per_lattice"])
@@ -148,6 +150,26 @@ def test_batch_autotune_restores_state(clbm):
         with clbm.Lattice(**p.kwargs(), dtype="f32") as ref:
             ref.step(101)
             _same(lt.get_state(), ref.get_state(), "f32")
+        lt.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s", "f16r"])
+def test_default_launch_within_form_tolerance(clbm, dtype):
+    # The batch's untuned default launch (register-capped for the FP32-math
+    # forms) against the lattices alone: the velocity bar of each form.
+    probs = _mix(3)
+    lats = [clbm.Lattice(**p.kwargs(), dtype=dtype, check_interval=50) for p in probs]
+    with clbm.Batch(dtype, capacity=8, check_interval=50) as b:
+        for lt in lats:
+            b.add(lt)
+        b.step(300)
+        got = [lt.fields()[1] for lt in lats]
+    tol = {"f64": 1e-12, "f32": 1e-4, "f16s": 2e-3, "f16r": 2e-3}[dtype]
+    for lt, p, u in zip(lats, probs, got):
+        with clbm.Lattice(**p.kwargs(), dtype=dtype, check_interval=50) as ref:
+            ref.step(300)
+            u_ref = ref.fields()[1]
+        assert np.linalg.norm(u - u_ref) <= tol * np.linalg.norm(u_ref)
         lt.close()
 
 
