@@ -23,7 +23,8 @@ struct LatDesc {
   int64_t qstride;
   int nx, ny, nz, pitch, plane;
   unsigned facebits;
-  int tiles_x, tiles_y, tile_begin;
+  int tiles_x, tiles_y;
+  int tw_log2;         // tile width (nodes along x) = 1 << tw_log2, height = threads / width
   int slot;            // row of this lattice in the batch's reduction array
   unsigned step_offset;  // F16R: lattice steps minus batch steps (seeds its rounding)
   R lidc[Q];
@@ -116,6 +117,8 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
     const LatDesc<R>& L = get(ok ? li : 0);
     if (ok)
       ok = L.buf[0] != nullptr && L.buf[1] != nullptr && tx < L.tiles_x && ty < L.tiles_y &&
+           L.tw_log2 >= 0 && L.tw_log2 <= 10 && (1 << L.tw_log2) <= int(blockDim.x * blockDim.y) &&
+           (int(blockDim.x * blockDim.y) & ((1 << L.tw_log2) - 1)) == 0 &&
            zc >= 1 && tz * zc < L.nz && L.pitch >= L.nx && L.plane == L.pitch * L.ny &&
            L.qstride >= int64_t(L.plane) * L.nz && 19 * L.qstride < (int64_t(1) << 31) &&
            (L.C.has_force != 0) == FORCE && (!REF || (L.ref[0] != nullptr && L.ref[1] != nullptr));
@@ -123,8 +126,11 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
       if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(&hdr->err, 1);
       continue;
     }
-    const int x = tx * blockDim.x + threadIdx.x;
-    const int y = ty * blockDim.y + threadIdx.y;
+    // the block's threads in row order over a tile of 2^tw_log2 x (threads
+    // >> tw_log2) nodes (the tile width is chosen per lattice)
+    const int lin = int(threadIdx.y * blockDim.x + threadIdx.x);
+    const int x = (tx << L.tw_log2) + (lin & ((1 << L.tw_log2) - 1));
+    const int y = ty * (int(blockDim.x * blockDim.y) >> L.tw_log2) + (lin >> L.tw_log2);
     const S* src = static_cast<const S*>(L.buf[parity]);
     S* dst = static_cast<S*>(const_cast<void*>(L.buf[parity ^ 1]));
     const bool active = x < L.nx && y < L.ny;
@@ -191,7 +197,7 @@ constexpr int BATCH_CONST_BYTES = 60 * 1024;
 template <typename R>
 void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur, const void* other,
                  const void* ref_cur, const void* ref_other, void* uprev, int tiles_x,
-                 int tiles_y, int tile_begin, int slot, unsigned step_offset) {
+                 int tiles_y, int tw_log2, int slot, unsigned step_offset) {
   LatDesc<R> L{};
   L.buf[0] = cur;
   L.buf[1] = other;
@@ -207,7 +213,7 @@ void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur,
   L.facebits = g.facebits;
   L.tiles_x = tiles_x;
   L.tiles_y = tiles_y;
-  L.tile_begin = tile_begin;
+  L.tw_log2 = tw_log2;
   L.slot = slot;
   L.step_offset = step_offset;
   for (int q = 0; q < Q; ++q)
@@ -261,8 +267,8 @@ void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur,
   int desc_capacity_##SUFFIX() { return int(BATCH_CONST_BYTES / sizeof(LatDesc<R>)); }         \
   void fill_desc_##SUFFIX(void* out, const Geom& g, const PhysParams& P, const void* cur,        \
                           const void* other, const void* ref_cur, const void* ref_other,       \
-                          void* uprev, int tx, int ty, int tb, int slot, unsigned so) {        \
-    fill_desc_t<R>(out, g, P, cur, other, ref_cur, ref_other, uprev, tx, ty, tb, slot, so);    \
+                          void* uprev, int tx, int ty, int twl, int slot, unsigned so) {       \
+    fill_desc_t<R>(out, g, P, cur, other, ref_cur, ref_other, uprev, tx, ty, twl, slot, so);   \
   }                                                                                            \
   cudaError_t upload_desc_##SUFFIX(const void* host, int base, int n) {                        \
     return cudaMemcpyToSymbol(c_lat_##SUFFIX, host, size_t(n) * sizeof(LatDesc<R>),            \

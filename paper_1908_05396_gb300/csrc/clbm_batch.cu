@@ -143,7 +143,7 @@ cudaError_t upload_desc(clbm_dtype t, const void* host, int base, int n) {
                           : upload_desc_f16(host, base, n);
 }
 
-void fill_desc(clbm_dtype t, void* out, const clbm_ctx* h, int tx, int ty, int tb, int slot,
+void fill_desc(clbm_dtype t, void* out, const clbm_ctx* h, int tx, int ty, int twl, int slot,
                unsigned so) {
   const void* cur = h->buf[h->cur];
   const void* other = h->buf[1 - h->cur];
@@ -151,13 +151,13 @@ void fill_desc(clbm_dtype t, void* out, const clbm_ctx* h, int tx, int ty, int t
   const void* rcur = h->ref[h->cur];
   const void* rother = h->ref[1 - h->cur];
   if (t == CLBM_F64)
-    fill_desc_f64(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot, so);
+    fill_desc_f64(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, twl, slot, so);
   else if (t == CLBM_F32)
-    fill_desc_f32(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot, so);
+    fill_desc_f32(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, twl, slot, so);
   else if (t == CLBM_F16R)
-    fill_desc_f16r(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot, so);
+    fill_desc_f16r(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, twl, slot, so);
   else
-    fill_desc_f16(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, tb, slot, so);
+    fill_desc_f16(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, twl, slot, so);
 }
 
 cudaError_t launch(clbm_batch_ctx* b, bool check) {
@@ -254,18 +254,22 @@ cudaError_t launch_lattices(clbm_batch_ctx* b, bool check, int flip) {
     double* acc = b->d_acc + 4 * size_t(s);
     CheckBufs cb{h->uprev, acc, reinterpret_cast<int*>(acc + 3)};
     const cudaStream_t st = pl_stream(b, b->stream_of[size_t(s)]);
+    // the lattice's own block: the tile width of the persistent kernel's rule
+    const int threads = int(b->pl_block.x * b->pl_block.y);
+    const int tw = tile_width(h->g.nx, int(h->elem), int(b->pl_block.x), threads);
+    const dim3 blk(unsigned(tw), unsigned(threads / tw), 1);
     cudaError_t e;
     if (h->in_place) {  // one buffer, the layout alternating with the steps
       const int lay = h->layout ^ flip;
       switch (b->dtype) {
         case CLBM_F64:
-          e = launch_step_aa_f64(h->buf[0], h->g, h->P, cb, check, b->pl_block, b->pl_npt, lay, st);
+          e = launch_step_aa_f64(h->buf[0], h->g, h->P, cb, check, blk, b->pl_npt, lay, st);
           break;
         case CLBM_F32:
-          e = launch_step_aa_f32(h->buf[0], h->g, h->P, cb, check, b->pl_block, b->pl_npt, lay, st);
+          e = launch_step_aa_f32(h->buf[0], h->g, h->P, cb, check, blk, b->pl_npt, lay, st);
           break;
         default:
-          e = launch_step_aa_f16(h->buf[0], h->g, h->P, cb, check, b->pl_block, b->pl_npt, lay, st);
+          e = launch_step_aa_f16(h->buf[0], h->g, h->P, cb, check, blk, b->pl_npt, lay, st);
           break;
       }
       if (e != cudaSuccess) return e;
@@ -276,13 +280,13 @@ cudaError_t launch_lattices(clbm_batch_ctx* b, bool check, int flip) {
     void* dst = h->buf[1 - c];
     switch (b->dtype) {
       case CLBM_F64:
-        e = launch_step_f64(src, dst, h->g, h->P, cb, check, b->pl_block, b->pl_npt, st);
+        e = launch_step_f64(src, dst, h->g, h->P, cb, check, blk, b->pl_npt, st);
         break;
       case CLBM_F32:
-        e = launch_step_f32(src, dst, h->g, h->P, cb, check, b->pl_block, b->pl_npt, st);
+        e = launch_step_f32(src, dst, h->g, h->P, cb, check, blk, b->pl_npt, st);
         break;
       default:
-        e = launch_step_f16(src, dst, h->g, h->P, cb, check, b->pl_block, b->pl_npt, st);
+        e = launch_step_f16(src, dst, h->g, h->P, cb, check, blk, b->pl_npt, st);
         break;
     }
     if (e != cudaSuccess) return e;
@@ -303,15 +307,20 @@ int upload(clbm_batch_ctx* b) {
       clbm_ctx* h = b->slots[s];
       // in-place lattices (mode 1 only) have no place in the tile tables
       if (!h || h->in_place || (h->P.has_force != 0) != (pass == 1)) continue;
-      const int tx = (h->g.nx + int(b->block.x) - 1) / int(b->block.x);
-      const int ty = (h->g.ny + int(b->block.y) - 1) / int(b->block.y);
+      const int threads = int(b->block.x * b->block.y);
+      const int tw = tile_width(h->g.nx, int(h->elem), int(b->block.x), threads);
+      int twl = 0;
+      while ((1 << twl) < tw) ++twl;
+      const int th = threads / tw;
+      const int tx = (h->g.nx + tw - 1) / tw;
+      const int ty = (h->g.ny + th - 1) / th;
       const int tz = (h->g.nz + b->zc - 1) / b->zc;   // chunks of zc planes
       if (tx > 255 || ty > 4095 || tz > 4095)
         return bfail(b, CLBM_ERR_UNSUPPORTED, "lattice has too many tiles for the batch table");
       // the lattice's step count minus the batch's: the kernels add the
       // batch's device-side count to recover the lattice's own
       const unsigned so = unsigned(uint64_t(h->steps) - uint64_t(b->steps));
-      fill_desc(b->dtype, stage + size_t(nlat) * b->desc_bytes, h, tx, ty, ntiles, s, so);
+      fill_desc(b->dtype, stage + size_t(nlat) * b->desc_bytes, h, tx, ty, twl, s, so);
       for (int kz = 0; kz < tz; ++kz)
         for (int ky = 0; ky < ty; ++ky)
           for (int kx = 0; kx < tx; ++kx) {

@@ -24,6 +24,23 @@ struct Geom {
   double rho0;
 };
 
+// Width (nodes along x) of the tiles of a lattice nx nodes wide, for blocks
+// of `threads` threads whose x extent is `bx`: bx, or the narrowest of 32,
+// 16, 8 below it whose padded row is at least 1/8 shorter than the wider
+// one's.  Narrow lattices (the 8-wide channels, 16..48-wide cavities) then
+// leave fewer lanes idle.  A row keeps at least 32 bytes (one DRAM sector) of
+// elements of `elem` bytes, and the width divides the block.
+inline int tile_width(int nx, int elem, int bx, int threads) {
+  int w = bx;
+  for (int c = 32; c >= 8; c /= 2) {
+    if (c >= w) continue;
+    if (c * elem < 32 || threads % c) break;
+    const int pw = (nx + w - 1) / w * w, pc = (nx + c - 1) / c * c;
+    if (8 * pc <= 7 * pw) w = c;
+  }
+  return w;
+}
+
 // Physical parameters of the collision (host precision; kernels convert).
 struct PhysParams {
   double rho0;
@@ -95,7 +112,8 @@ struct BatchHeader {
   cudaError_t upload_desc_##SUFFIX(const void* host, int base, int n);                          \
   void fill_desc_##SUFFIX(void* out, const Geom& g, const PhysParams& P, const void* cur,       \
                           const void* other, const void* ref_cur, const void* ref_other,      \
-                          void* uprev, int tx, int ty, int tb, int slot, unsigned step_offset);
+                          void* uprev, int tx, int ty, int tw_log2, int slot,               \
+                          unsigned step_offset);
 CLBM_DECLARE_BATCH(f64)
 CLBM_DECLARE_BATCH(f32)
 CLBM_DECLARE_BATCH(f16)
