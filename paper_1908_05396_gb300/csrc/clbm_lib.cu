@@ -234,7 +234,8 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
   for (int a = 0; a < 3; ++a) g.U[a] = U[a];
   g.rho0 = rho0;
   fill_params(h->P, K, n, body_force, rho0, nu_min, nu_max, dtype);
-  h->block.x = d->nx <= 32 ? 32 : d->nx <= 64 ? 64 : 128;
+  h->block.x = d->nx <= 32 ? unsigned(tile_width(d->nx, int(h->elem), 32, 128))
+                           : d->nx <= 64 ? 64 : 128;
   h->block.y = 128 / h->block.x;
   h->block.z = 1;
   h->npt = 1;  // the autotuner may switch to two nodes per thread
@@ -529,6 +530,11 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
         if (sh[0] > 32 && sh[0] > h->g.pitch) continue;
         cands.push_back({sh[0], sh[1], np + 4 * capped});
       }
+  // a lattice narrower than a warp: blocks as wide as its tile width
+  const int tw = tile_width(h->g.nx, int(h->elem), 32, 64);
+  if (tw < 32)
+    for (int capped = 0; capped <= 1; ++capped)
+      for (int t : {64, 128, 256}) cands.push_back({tw, t / tw, 1 + 4 * capped});
   // FP32 and FP16 storage: the TMA-staged kernel in each of its shapes
   if ((h->dtype == CLBM_F32 || h->dtype == CLBM_F16S) && !h->in_place)
     for (int v = 0; v < TMA_NVAR; ++v) cands.push_back({tma_bx(v), tma_by(v), TMA_NPT + 32 * v});
