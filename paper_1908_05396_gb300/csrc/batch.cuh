@@ -93,9 +93,10 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
                                             const unsigned* __restrict__ coord,
                                             BatchHeader* hdr, int parity, double* acc, int zc) {
   // tiles [0, ntiles0) belong to lattices without force, [ntiles0, ntiles) with
-  // F16R: the batch's step count, advanced at the end of every step by the
-  // last CTA of the forced launch (the second launch of each step)
-  const unsigned bstep = REF ? *reinterpret_cast<volatile const unsigned*>(&hdr->step) : 0u;
+  // F16R: this chain's step count, advanced at the end of each of its
+  // launches by the launch's last CTA
+  const unsigned bstep =
+      REF ? *reinterpret_cast<volatile const unsigned*>(&hdr->step[FORCE ? 1 : 0]) : 0u;
   const int t0 = FORCE ? hdr->ntiles0 : 0;
   const int t1 = FORCE ? hdr->ntiles : hdr->ntiles0;
   const int nlat = hdr->nlat;
@@ -175,15 +176,15 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
         atomicOr(reinterpret_cast<int*>(&a[3]), 1);
     }
   }
-  if constexpr (REF && FORCE) {
-    // every CTA of this step's last launch has read the step count: the last
-    // one to finish advances it
+  if constexpr (REF) {
+    // every CTA of this launch has read its chain's step count: the last one
+    // to finish advances it
     __syncthreads();
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       __threadfence();
-      if (atomicAdd(&hdr->done, 1) == int(gridDim.x) - 1) {
-        atomicExch(&hdr->done, 0);
-        atomicAdd(&hdr->step, 1u);
+      if (atomicAdd(&hdr->done[FORCE ? 1 : 0], 1) == int(gridDim.x) - 1) {
+        atomicExch(&hdr->done[FORCE ? 1 : 0], 0);
+        atomicAdd(&hdr->step[FORCE ? 1 : 0], 1u);
       }
     }
   }
@@ -239,26 +240,27 @@ void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur,
   }                                                                                            \
   cudaError_t launch_batch_##SUFFIX(int base, const int* owner, const unsigned* coord,         \
                                     const void* hdr, int parity, bool check, double* acc,      \
-                                    int zc, dim3 block, int grid, cudaStream_t st) {           \
+                                    int zc, dim3 block, int grid, cudaStream_t st,             \
+                                    cudaStream_t stf) {                                         \
     BatchHeader* H = static_cast<BatchHeader*>(const_cast<void*>(hdr));                        \
     const bool cap = grid < 0;                                                                 \
     if (cap) grid = -grid;                                                                     \
-    /* tiles without force, then tiles with force (an empty range exits at once) */           \
+    /* tiles without force on st, tiles with force on stf (an empty range exits at once) */   \
     if (check) {                                                                               \
       if (cap) {                                                                               \
         batch_kernel_##SUFFIX<true, true, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
-        batch_kernel_##SUFFIX<true, true, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<true, true, true><<<grid, block, 0, stf>>>(base, owner, coord, H, parity, acc, zc); \
       } else {                                                                                 \
         batch_kernel_##SUFFIX<true, false, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
-        batch_kernel_##SUFFIX<true, false, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<true, false, true><<<grid, block, 0, stf>>>(base, owner, coord, H, parity, acc, zc); \
       }                                                                                        \
     } else {                                                                                   \
       if (cap) {                                                                               \
         batch_kernel_##SUFFIX<false, true, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
-        batch_kernel_##SUFFIX<false, true, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<false, true, true><<<grid, block, 0, stf>>>(base, owner, coord, H, parity, acc, zc); \
       } else {                                                                                 \
         batch_kernel_##SUFFIX<false, false, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
-        batch_kernel_##SUFFIX<false, false, true><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<false, false, true><<<grid, block, 0, stf>>>(base, owner, coord, H, parity, acc, zc); \
       }                                                                                        \
     }                                                                                          \
     return cudaGetLastError();                                                                 \

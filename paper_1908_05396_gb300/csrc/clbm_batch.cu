@@ -160,21 +160,26 @@ void fill_desc(clbm_dtype t, void* out, const clbm_ctx* h, int tx, int ty, int t
     fill_desc_f16(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, twl, slot, so);
 }
 
+// One step of the persistent kernel: the unforced lattices' launch on
+// `stream`, the forced lattices' on the first extra stream.  The two touch
+// disjoint lattices, so between fork_streams(b, 2) and join_streams(b, 2) they
+// run concurrently, each chain in step order.
 cudaError_t launch(clbm_batch_ctx* b, bool check) {
   const int grid = b->blocks_per_sm * b->sms * (b->cap ? -1 : 1);
+  const cudaStream_t sf = b->aux[0];
   switch (b->dtype) {
     case CLBM_F64:
       return launch_batch_f64(b->desc_base, b->d_owner, b->d_coord, b->d_hdr, b->parity, check,
-                              b->d_acc, b->zc, b->block, grid, b->stream);
+                              b->d_acc, b->zc, b->block, grid, b->stream, sf);
     case CLBM_F32:
       return launch_batch_f32(b->desc_base, b->d_owner, b->d_coord, b->d_hdr, b->parity, check,
-                              b->d_acc, b->zc, b->block, grid, b->stream);
+                              b->d_acc, b->zc, b->block, grid, b->stream, sf);
     case CLBM_F16R:
       return launch_batch_f16r(b->desc_base, b->d_owner, b->d_coord, b->d_hdr, b->parity, check,
-                               b->d_acc, b->zc, b->block, grid, b->stream);
+                               b->d_acc, b->zc, b->block, grid, b->stream, sf);
     default:
       return launch_batch_f16(b->desc_base, b->d_owner, b->d_coord, b->d_hdr, b->parity, check,
-                              b->d_acc, b->zc, b->block, grid, b->stream);
+                              b->d_acc, b->zc, b->block, grid, b->stream, sf);
   }
 }
 
@@ -226,18 +231,18 @@ void assign_streams(clbm_batch_ctx* b) {
   }
 }
 
-// The extra streams wait for everything queued on `stream` so far.
-cudaError_t fork_streams(clbm_batch_ctx* b) {
+// The first n - 1 extra streams wait for everything queued on `stream` so far.
+cudaError_t fork_streams(clbm_batch_ctx* b, int n) {
   cudaError_t e = cudaEventRecord(b->ev[0], b->stream);
-  for (int k = 1; k < b->pl_streams && e == cudaSuccess; ++k)
+  for (int k = 1; k < n && e == cudaSuccess; ++k)
     e = cudaStreamWaitEvent(b->aux[size_t(k - 1)], b->ev[0], 0);
   return e;
 }
 
-// `stream` waits for everything queued on the extra streams so far.
-cudaError_t join_streams(clbm_batch_ctx* b) {
+// `stream` waits for everything queued on the first n - 1 extra streams so far.
+cudaError_t join_streams(clbm_batch_ctx* b, int n) {
   cudaError_t e = cudaSuccess;
-  for (int k = 1; k < b->pl_streams && e == cudaSuccess; ++k) {
+  for (int k = 1; k < n && e == cudaSuccess; ++k) {
     e = cudaEventRecord(b->ev[size_t(k)], b->aux[size_t(k - 1)]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev[size_t(k)], 0);
   }
@@ -343,7 +348,8 @@ int upload(clbm_batch_ctx* b) {
     b->owner_cap = cap;
     drop_graph(b);  // the graph holds the old table address
   }
-  BatchHeader hdr{nlat, ntiles, ntiles0, 0, unsigned(uint64_t(b->steps)), 0};
+  const unsigned st0 = unsigned(uint64_t(b->steps));
+  BatchHeader hdr{nlat, ntiles, ntiles0, 0, {st0, st0}, {0, 0}};
   if (nlat) BCK(b, upload_desc(b->dtype, stage, b->desc_base, nlat));
   if (ntiles) {
     BCK(b, cudaMemcpy(b->d_owner, b->h_owner.data(), size_t(ntiles) * sizeof(int),
@@ -378,11 +384,13 @@ int one_step(clbm_batch_ctx* b) {
   const bool check = ((b->steps + 1) % b->check_interval) == 0;
   if (check) BCK(b, cudaMemsetAsync(b->d_acc, 0, size_t(b->capacity) * 4 * sizeof(double), b->stream));
   if (b->mode == 1) {
-    BCK(b, fork_streams(b));
+    BCK(b, fork_streams(b, b->pl_streams));
     BCK(b, launch_lattices(b, check, 0));
-    BCK(b, join_streams(b));
+    BCK(b, join_streams(b, b->pl_streams));
   } else {
+    BCK(b, fork_streams(b, 2));
     BCK(b, launch(b, check));
+    BCK(b, join_streams(b, 2));
   }
   b->parity ^= 1;
   if (check) {
@@ -406,29 +414,31 @@ int capture(clbm_batch_ctx* b) {
     // Only the last step's check writes the sums: clear them up front, so
     // that the streams stay forked for the whole interval.
     e = cudaMemsetAsync(b->d_acc, 0, size_t(b->capacity) * 4 * sizeof(double), b->stream);
-    if (e == cudaSuccess) e = fork_streams(b);
+    if (e == cudaSuccess) e = fork_streams(b, b->pl_streams);
     for (int k = 0; k < b->check_interval && e == cudaSuccess; ++k)
       e = launch_lattices(b, k == b->check_interval - 1, k & 1);
-    if (e == cudaSuccess) e = join_streams(b);
+    if (e == cudaSuccess) e = join_streams(b, b->pl_streams);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(b->h_acc, b->d_acc, size_t(b->capacity) * 4 * sizeof(double),
                           cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(b->check_done, b->stream);
   }
-  int par = 0;
-  for (int k = 0; k < b->check_interval && e == cudaSuccess && b->mode == 0; ++k) {
-    const bool check = k == b->check_interval - 1;
-    if (check)
-      e = cudaMemsetAsync(b->d_acc, 0, size_t(b->capacity) * 4 * sizeof(double), b->stream);
+  if (b->mode == 0) {
+    // as in mode 1: the sums are cleared up front, so that the two chains stay
+    // forked for the whole interval
+    e = cudaMemsetAsync(b->d_acc, 0, size_t(b->capacity) * 4 * sizeof(double), b->stream);
+    if (e == cudaSuccess) e = fork_streams(b, 2);
     const int keep = b->parity;
-    b->parity = par;
-    if (e == cudaSuccess) e = launch(b, check);
+    for (int k = 0; k < b->check_interval && e == cudaSuccess; ++k) {
+      b->parity = k & 1;
+      e = launch(b, k == b->check_interval - 1);
+    }
     b->parity = keep;
-    par ^= 1;
-    if (check && e == cudaSuccess)
+    if (e == cudaSuccess) e = join_streams(b, 2);
+    if (e == cudaSuccess)
       e = cudaMemcpyAsync(b->h_acc, b->d_acc, size_t(b->capacity) * 4 * sizeof(double),
                           cudaMemcpyDeviceToHost, b->stream);
-    if (check && e == cudaSuccess) e = cudaEventRecord(b->check_done, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->check_done, b->stream);
   }
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
   if (e == cudaSuccess) e = e2;
@@ -521,6 +531,7 @@ int clbm_batch_create(clbm_dtype dtype, int capacity, int check_interval, void* 
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&b->h_acc), size_t(capacity) * 4 * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_stage, size_t(capacity) * b->desc_bytes);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->check_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = ensure_streams(b, 2);  // the forced lattices' chain
   if (e == cudaSuccess) std::memset(b->h_acc, 0, size_t(capacity) * 4 * sizeof(double));
   if (e != cudaSuccess) {
     std::string m = std::string("clbm_batch_create: ") + cudaGetErrorString(e);
@@ -722,15 +733,19 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
         b->blocks_per_sm = bp;
         b->dirty = true;
         if (upload(b) != CLBM_OK) { err = cudaErrorUnknown; break; }
+        err = fork_streams(b, 2);
         for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
           err = launch(b, false);
           b->parity ^= 1;
         }
+        if (err == cudaSuccess) err = join_streams(b, 2);
         if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
+        if (err == cudaSuccess) err = fork_streams(b, 2);
         for (int k = 0; k < steps && err == cudaSuccess; ++k) {
           err = launch(b, false);
           b->parity ^= 1;
         }
+        if (err == cudaSuccess) err = join_streams(b, 2);
         if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
         if (err == cudaSuccess) err = cudaEventSynchronize(e1);
         float ms = 0.0f;
@@ -761,19 +776,19 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
           b->pl_streams = ns;
           b->dirty = true;
           if (upload(b) != CLBM_OK) { err = cudaErrorUnknown; break; }
-          err = fork_streams(b);
+          err = fork_streams(b, b->pl_streams);
           for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
             err = launch_lattices(b, false, b->parity);
             b->parity ^= 1;
           }
-          if (err == cudaSuccess) err = join_streams(b);
+          if (err == cudaSuccess) err = join_streams(b, b->pl_streams);
           if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
-          if (err == cudaSuccess) err = fork_streams(b);
+          if (err == cudaSuccess) err = fork_streams(b, b->pl_streams);
           for (int k = 0; k < steps && err == cudaSuccess; ++k) {
             err = launch_lattices(b, false, b->parity);
             b->parity ^= 1;
           }
-          if (err == cudaSuccess) err = join_streams(b);
+          if (err == cudaSuccess) err = join_streams(b, b->pl_streams);
           if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
           if (err == cudaSuccess) err = cudaEventSynchronize(e1);
           float ms = 0.0f;

@@ -95,18 +95,22 @@ __host__ __device__ constexpr int tma_by(int v) {
 void set_unbound_error(const char* msg);
 
 // Batched step (batch.cuh): descriptors are opaque bytes to the host code.
+// The unforced and the forced lattices form two independent chains of
+// launches (on two streams), so each chain counts its own steps.
 struct BatchHeader {
   int nlat;
   int ntiles;   // all tiles
-  int ntiles0;  // tiles of lattices without body force (they come first)
+  int ntiles0;  // tiles of lattices without force (they come first)
   int err;      // set by the kernel if a tile's descriptor fails its checks
-  unsigned step;  // batch steps done (F16R: the kernels derive each lattice's step)
-  int done;       // F16R: CTAs of the forced launch finished in this step
+  unsigned step[2];  // steps done by the unforced [0] / forced [1] chain (F16R: each
+                     // lattice's step is its chain's count plus an offset)
+  int done[2];       // F16R: CTAs of that chain's current launch that finished
 };
 #define CLBM_DECLARE_BATCH(SUFFIX)                                                              \
   cudaError_t launch_batch_##SUFFIX(int base, const int* owner, const unsigned* coord,         \
                                     const void* hdr, int parity, bool check, double* acc,       \
-                                    int zc, dim3 block, int grid, cudaStream_t st);             \
+                                    int zc, dim3 block, int grid, cudaStream_t st,              \
+                                    cudaStream_t st_forced);                                    \
   size_t desc_size_##SUFFIX();                                                                  \
   int desc_capacity_##SUFFIX();                                                                 \
   cudaError_t upload_desc_##SUFFIX(const void* host, int base, int n);                          \
