@@ -60,12 +60,13 @@ extern "C" {
  *   CLBM_F16S : (f - w rho0) * 1024 stored in FP16 (round to nearest even),
  *               collision in FP32.
  *   CLBM_F16R : (f - w [rho0 + drho + 3 (rho0 + drho)(e . u)]) * 1024 in
- *               FP16, relative to the writing node's own (drho, u), which is
- *               stored beside the populations as four FP16 values; collision
- *               in FP32.  Removing the first-order equilibrium before
- *               rounding keeps steady states close to FP64.  16 more bytes
- *               per node update than F16S.  Not available to clbm_batch_* or
- *               clbm_step_noalloc.
+ *               FP16 with stochastic rounding, relative to the writing node's
+ *               own (drho, 3 (rho0 + drho) u), which is stored beside the
+ *               populations as four FP16 values; collision in FP32.  Removing
+ *               the first-order equilibrium before rounding keeps steady
+ *               states close to FP64.  16 more bytes per node update than
+ *               F16S.  Not available to clbm_step_noalloc, to in-place
+ *               streaming or to a batch's one-launch-per-lattice mode.
  * Residual and mass reductions accumulate in FP64 for every form. */
 typedef enum { CLBM_F64 = 0, CLBM_F32 = 1, CLBM_F16S = 2, CLBM_F16R = 3 } clbm_dtype;
 

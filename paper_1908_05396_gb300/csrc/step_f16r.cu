@@ -1,10 +1,10 @@
 // step_f16r.cu -- kernels of the F16R storage form: FP16 populations stored
 // relative to the writing node's first-order equilibrium.
 //
-// Each node keeps a reference (rho - rho0, u) of its last collision as four
-// FP16 values next to its populations, and stores
+// Each node keeps a reference (rho - rho0, 3 rho u) of its last collision as
+// four FP16 values next to its populations, and stores
 //     s_q = fp16( 1024 * ( f~_q - w_q rho0 - r_q ) ),
-//     r_q = w_q [ drho + 3 (rho0 + drho) (e_q . u) ]        (reference values),
+//     r_q = w_q [ drho + e_q . v ],  v = 3 (rho0 + drho) u  (reference values),
 // which removes the rest value and the first-order (velocity) part of the
 // equilibrium, the largest parts of f~, before FP16 rounding (stochastic in
 // the step kernels, see enc16_sr).  A reader
@@ -19,7 +19,7 @@ namespace clbm {
 namespace {
 
 struct Ref4 {
-  float dr, ux, uy, uz;
+  float dr, vx, vy, vz;  // rho - rho0 and v = 3 rho u, as stored (FP16)
 };
 
 __device__ __forceinline__ Ref4 ref_load(const uint2* p) {
@@ -29,9 +29,11 @@ __device__ __forceinline__ Ref4 ref_load(const uint2* p) {
   return {a.x, a.y, b.x, b.y};
 }
 
-// Round (drho, u) to FP16 for storage; r receives the rounded values.
-__device__ __forceinline__ uint2 ref_pack(float dr, float ux, float uy, float uz, Ref4& r) {
-  const __half2 a = __floats2half2_rn(dr, ux), b = __floats2half2_rn(uy, uz);
+// Round (drho, 3 rho u) to FP16 for storage; r receives the rounded values.
+__device__ __forceinline__ uint2 ref_pack(float dr, float ux, float uy, float uz, float rho0,
+                                          Ref4& r) {
+  const float r3 = 3.0f * (rho0 + dr);
+  const __half2 a = __floats2half2_rn(dr, r3 * ux), b = __floats2half2_rn(r3 * uy, r3 * uz);
   const float2 fa = __half22float2(a), fb = __half22float2(b);
   r = {fa.x, fa.y, fb.x, fb.y};
   uint2 v;
@@ -40,10 +42,12 @@ __device__ __forceinline__ uint2 ref_pack(float dr, float ux, float uy, float uz
   return v;
 }
 
-// First-order equilibrium deviation of direction q about the reference.
-__device__ __forceinline__ float ref_term(int q, const Ref4& r, float rho0) {
-  const float eu = float(cx(q)) * r.ux + float(cy(q)) * r.uy + float(cz(q)) * r.uz;
-  return wt<float>(q) * (r.dr + 3.0f * (rho0 + r.dr) * eu);
+// First-order equilibrium deviation of direction q about the reference,
+// w_q [drho + 3 rho (e_q . u)]: the stored v = 3 rho u saves the product per
+// direction (rho0 is carried in v).
+__device__ __forceinline__ float ref_term(int q, const Ref4& r, float /*rho0*/) {
+  const float ev = float(cx(q)) * r.vx + float(cy(q)) * r.vy + float(cz(q)) * r.vz;
+  return wt<float>(q) * (r.dr + ev);
 }
 
 __device__ __forceinline__ float dec16(__half v) { return __half2float(v) * float(1.0 / F16_SCALE); }
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
     NodeOut<float> o;
     collide<float, FORCE>(a.C, d, o);
     Ref4 rr;
-    r.ref_dst[i] = ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rr);
+    r.ref_dst[i] = ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rho0, rr);
     uint32_t rs = sr_seed(uint32_t(i), r.step);
 #pragma unroll
     for (int q = 0; q < Q; ++q) a.dstq[q][i] = enc16_sr(d[q] - ref_term(q, rr, rho0), rs);
@@ -257,7 +261,7 @@ __global__ void import_ref_kernel(const double* __restrict__ in, Geom g, float r
     jz += cz(q) * f[q];
   }
   Ref4 rr;
-  ref[i] = ref_pack(float(rho - rho0), float(jx / rho), float(jy / rho), float(jz / rho), rr);
+  ref[i] = ref_pack(float(rho - rho0), float(jx / rho), float(jy / rho), float(jz / rho), rho0, rr);
 #pragma unroll
   for (int q = 0; q < Q; ++q)
     dst[q * g.qstride + i] =
@@ -283,7 +287,7 @@ __global__ void collide_nodes_ref_kernel(CollideConst<float> C, const double* __
     jz += cz(q) * v;
   }
   Ref4 rr;
-  ref_pack(float(r0 - rho0), float(jx / r0), float(jy / r0), float(jz / r0), rr);
+  ref_pack(float(r0 - rho0), float(jx / r0), float(jy / r0), float(jz / r0), rho0, rr);
   float d[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
@@ -292,7 +296,7 @@ __global__ void collide_nodes_ref_kernel(CollideConst<float> C, const double* __
   }
   NodeOut<float> o;
   collide<float, FORCE>(C, d, o);
-  ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rr);
+  ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rho0, rr);
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const float t = ref_term(q, rr, rho0);
@@ -356,7 +360,7 @@ __device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y
   }
   collide<float, FORCE>(L.C, d, o);
   Ref4 rr;
-  rd[i] = ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rr);
+  rd[i] = ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rho0, rr);
   uint32_t rst = sr_seed(uint32_t(i), step);
 #pragma unroll
   for (int q = 0; q < Q; ++q) dst[q * qs + i] = enc16_sr(d[q] - ref_term(q, rr, rho0), rst);
