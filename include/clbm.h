@@ -217,8 +217,10 @@ int clbm_set_rates(clbm_handle h, const double omega[10]);
 
 /* ---- Batched stepping of many lattices --------------------------------
  * Not in the paper: a batch steps up to `capacity` lattices of one storage
- * form (any of the four, F16R with its reference moments) together, one launch of a persistent kernel per time step for all of
- * them (tiles of every lattice from a device-side table), with each whole
+ * form (any of the four, F16R with its reference moments) together: per
+ * time step one launch of a persistent kernel over the tiles of all
+ * lattices without body force and one over those with it, the two on two
+ * streams at once (tiles from a device-side table), with each whole
  * check interval queued as one CUDA graph (or, after
  * clbm_batch_set_lattice_launch, one launch per lattice within that graph).  Lattices join and leave between
  * clbm_batch_step() calls; each keeps its own buffers, parameters, step

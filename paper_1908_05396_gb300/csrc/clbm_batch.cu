@@ -1,11 +1,12 @@
 // clbm_batch.cu -- host side of the batched multi-lattice step (include/clbm.h).
 //
 // A batch holds up to `capacity` lattices (clbm_handle) of one storage form
-// and steps them together: one launch of the persistent batch kernel per time
-// step, for all of them.  Whole check intervals run as one CUDA graph captured
-// on first use: (check_interval - 1) plain launches of alternating parity,
-// then a check launch whose per-lattice FP64 sums are copied to pinned host
-// memory.  The kernel reads its tile table and lattice descriptors from device
+// and steps them together: per time step, one launch of the persistent batch
+// kernel over the lattices without body force and one over those with it, on
+// two streams (the two launches touch disjoint lattices).  Whole check
+// intervals run as one CUDA graph captured on first use: (check_interval - 1)
+// plain steps of alternating parity, then a check step whose per-lattice FP64
+// sums are copied to pinned host memory.  The kernel reads its tile table and lattice descriptors from device
 // memory, so the graph stays valid when lattices join or leave; only a change
 // of launch shape or of the table's capacity recaptures it.
 //
