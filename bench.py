@@ -30,7 +30,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS & % HBM roofline, FP64 vs FP32/FP16-store; served solves/s, p50/p99"
-BYTES_PER_POP = {"f64": 8, "f32": 4, "f16s": 2}
+BYTES_PER_POP = {"f64": 8, "f32": 4, "f16s": 2, "f16r": 2}
+# algorithmic bytes per lattice update: 19 reads + 19 writes of the stored
+# type; F16R also reads and writes its node's 8-byte FP16 reference
+BYTES_PER_UPDATE = {"f64": 304, "f32": 152, "f16s": 76, "f16r": 92}
 L_BENCH = 128
 RE_BENCH = 100.0
 NS_BENCH = (0.5, 1.0, 1.5)
@@ -334,9 +337,9 @@ def run_ours(args):
 
     # ---- the other forms ------------------------------------------------------
     forms = {}
-    form_steps = {"f64": max(3, args.steps // 40), "f16s": args.steps}
+    form_steps = {"f64": max(3, args.steps // 40), "f16s": args.steps, "f16r": args.steps}
     form_steps["f32_inplace"] = args.steps
-    for name in ("f64", "f16s", "f32_inplace"):
+    for name in ("f64", "f16s", "f16r", "f32_inplace"):
         if args.forms and name not in args.forms:
             continue
         dt, ip = (name[:-len("_inplace")], True) if name.endswith("_inplace") else (name, False)
@@ -344,9 +347,9 @@ def run_ours(args):
         ms_f, N_f, launches_f, tuned_f = _time_form(clbm, torch, dt, form_steps[name], args.warmup,
                                                     stream, in_place=ip)
         mlups = N_f * len(NS_BENCH) * form_steps[name] / (ms_f * 1e-3) / 1e6
-        gbs = 38 * BYTES_PER_POP[dt] * N_f * launches_f / (ms_f * 1e-3) / 1e9
+        gbs = BYTES_PER_UPDATE[dt] * N_f * launches_f / (ms_f * 1e-3) / 1e9
         forms[name] = {"MLUPS": mlups, "GB/s": gbs, "frac_of_hbm": gbs / peak,
-                       "steps": form_steps[name], "bytes_per_update": 38 * BYTES_PER_POP[dt],
+                       "steps": form_steps[name], "bytes_per_update": BYTES_PER_UPDATE[dt],
                        "launch": [(t["block"], t["npt"]) for t in tuned_f]}
         if ip:
             forms[name]["what"] = "one population buffer streamed in place (half the memory)"
