@@ -156,6 +156,7 @@ struct StepArgs {
   int64_t qstride;
   int nx, ny, nz, pitch, plane;
   unsigned facebits;
+  int zrev;          // 1: planes in descending z (every other step, see launch_step_t)
   R lidc[Q];         // 6 w_q rho0 (e_q . U_lid): lid momentum correction
   CollideConst<R> C;
   CheckBufs cb;
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_kernel(const StepArgs<S
   pdl_enter();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int z = a.zrev ? a.nz - 1 - int(blockIdx.z) : int(blockIdx.z);
   const bool active = x < a.nx && y < a.ny;
   if (!CHECK && !active) return;
   double du2 = 0.0, uu = 0.0, dr = 0.0;
@@ -542,6 +543,11 @@ cudaError_t launch_step_t(const void* src, void* dst, const Geom& g, const PhysP
   a.pitch = g.pitch;
   a.plane = int(g.plane);
   a.facebits = g.facebits;
+  // Blocks run roughly in launch order, z planes last, so a step ends with
+  // its highest planes still in L2.  Sweeping z downward on every other step
+  // (the steps that write the lower-addressed of the two buffers) makes the
+  // next step read those planes first, from L2.
+  a.zrev = reinterpret_cast<uintptr_t>(dst) < reinterpret_cast<uintptr_t>(src) ? 1 : 0;
   a.C = make_const<R>(P);
   a.cb = cb;
   // npt: 1 or 2 nodes per thread; +4 selects the register-capped variant;

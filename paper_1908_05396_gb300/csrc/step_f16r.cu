@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
   pdl_enter();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
+  const int z = a.zrev ? a.nz - 1 - int(blockIdx.z) : int(blockIdx.z);  // as step_kernel
   const bool active = x < a.nx && y < a.ny;
   if (!CHECK && !active) return;
   const float rho0 = a.C.rho0;
@@ -385,6 +385,7 @@ cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, vo
   lid_table(g, a.lidc);
   r.ref_src = rs;
   r.ref_dst = static_cast<uint2*>(ref_dst);
+  a.zrev = reinterpret_cast<uintptr_t>(dst) < reinterpret_cast<uintptr_t>(src) ? 1 : 0;
   a.src = s;
   a.qstride = g.qstride;
   a.nx = g.nx;
