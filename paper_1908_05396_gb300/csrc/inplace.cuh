@@ -288,7 +288,7 @@ cudaError_t launch_step_aa_t(void* buf, const Geom& g, const PhysParams& P, cons
   StepArgs<S, R> a;
   S* A = static_cast<S*>(buf);
   const uintptr_t base = reinterpret_cast<uintptr_t>(A);
-  a.zrev = 0;  // the alternating sweep of step_kernel measured 2 % slower here
+  a.zrev = 0;  // an alternating sweep (either parity) measured 2 % slower here
   for (int q = 0; q < Q; ++q) {
     const int64_t off = int64_t(cz(q)) * g.plane + int64_t(cy(q)) * g.pitch + cx(q);
     // address arithmetic through integers: a shifted base may lie outside the
