@@ -79,3 +79,24 @@ def test_reference_arm_rank0_prints_one_contract_line(monkeypatch, capsys):
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_clamp_count_classifies_nodes():
+    import numpy as np
+
+    class Lat:
+        def __init__(self, rho, gd):
+            self.rho, self.gd = rho, gd
+
+        def fields(self):
+            return self.rho, None, self.gd
+
+    class Prob:
+        K, n = 0.01, 0.5
+
+    rho = np.ones(5)
+    # nu = K / rho * gd^(n - 1): gd = 0 -> inf (nu_max), 4e4 -> 5e-5 (below nu_min),
+    # 1 -> 1e-2 (free), 1e-5 -> 3.2 (free), 1e-7 -> 31.6 (above nu_max)
+    gd = np.array([0.0, 4e4, 1.0, 1e-5, 1e-7])
+    got = bench._clamp_active_nodes([Lat(rho, gd)], [Prob()])
+    assert got == {"at_nu_min": 1, "at_nu_max": 2}

@@ -76,3 +76,18 @@ def test_stability_limit_f64_matches_oracle(oracle):
         assert abs(g[0] - r[0]) <= step * (1 + 1e-9), (gpu, ref)
     # over-relaxed third and fourth orders lower the limit
     assert ref[2][1] <= ref[0][0]
+
+
+def test_bisection_edge_cases():
+    calls = []
+    assert st.max_lid_velocity([], _fake_runner({}, calls), rounds=4) == []
+    c = st.Case(1.0, 0.6)
+    calls = []
+    # stable at the upper end: no bisection runs
+    assert st.max_lid_velocity([c], _fake_runner({c: 1.0}, calls), u_hi=0.25, rounds=6) == \
+        [(0.25, None)]
+    assert calls == [1]
+    # unstable even near rest: the bracket closes on 0
+    calls = []
+    lo, hi = st.max_lid_velocity([c], _fake_runner({c: 0.0}, calls), u_hi=0.25, rounds=3)[0]
+    assert lo == 0.0 and hi == 0.25 / 8 and calls == [1, 1, 1, 1]
