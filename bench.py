@@ -704,7 +704,11 @@ STABILITY_RATES = {
     "w9=1.5": (1.5,) + (1.0,) * 9,
     "w10-18=0.8": (1.0,) + (0.8,) * 9,              # under-relaxed 3rd/4th orders
     "w10-18=1.2": (1.0,) + (1.2,) * 9,              # over-relaxed 3rd/4th orders
+    "w10-18=1.1": (1.0,) + (1.1,) * 9,
+    "w10-18=1.3": (1.0,) + (1.3,) * 9,
+    "w10-18=1.4": (1.0,) + (1.4,) * 9,
 }
+STABILITY_DEFAULT_SETS = ("unit", "w9=0.5", "w9=1.5", "w10-18=0.8", "w10-18=1.2")
 
 
 def run_stability(args):
@@ -718,8 +722,9 @@ def run_stability(args):
     from paper_1908_05396_gb300 import build
     build.build()
     from paper_1908_05396_gb300 import stability as st
-    cases = [st.Case(n, tau, rates, label) for label, rates in STABILITY_RATES.items()
-             for n in (0.8, 1.0, 1.5) for tau in args.stability_tau]
+    sets = args.stability_sets or STABILITY_DEFAULT_SETS
+    cases = [st.Case(n, tau, STABILITY_RATES[label], label) for label in sets
+             for n in args.stability_n for tau in args.stability_tau]
     t0 = time.perf_counter()
     run = st.batch_runner(args.stability_L, args.stability_steps, args.stability_dtype)
     res = st.max_lid_velocity(cases, run, u_hi=args.stability_uhi, rounds=args.stability_rounds)
@@ -858,6 +863,9 @@ def main():
     ap.add_argument("--stability-L", type=int, default=64)
     ap.add_argument("--stability-steps", type=int, default=50_000)
     ap.add_argument("--stability-tau", type=float, nargs="*", default=[0.505, 0.51, 0.52, 0.55])
+    ap.add_argument("--stability-sets", nargs="*", default=None, choices=list(STABILITY_RATES),
+                    help="rate sets to sweep (default: the five of the committed table)")
+    ap.add_argument("--stability-n", type=float, nargs="*", default=[0.8, 1.0, 1.5])
     ap.add_argument("--stability-uhi", type=float, default=0.25,
                     help="upper end of the bisection (the library takes |U_lid| < 0.3)")
     ap.add_argument("--stability-rounds", type=int, default=8)
