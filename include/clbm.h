@@ -176,7 +176,8 @@ typedef void (*clbm_free_fn)(void* ptr, size_t bytes, int device, void* stream, 
 int clbm_set_allocator(clbm_alloc_fn alloc_fn, clbm_free_fn free_fn, void* user);
 
 /* Pick the launch shape of h's step kernel by timing: thread-block shapes
- * from 32x1 to 256x1 and, for the FP32-math forms, one or two nodes per
+ * from 32x1 to 256x1 (and, for a lattice narrower than a warp, blocks 8 or
+ * 16 wide) and, for the FP32-math forms, one or two nodes per
  * thread (two nodes are collided together with packed FP32 instructions),
  * with and without a 64-register cap; for FP32 and F16S storage also the
  * TMA-staged kernel in each of its shapes (see clbm_set_launch).
