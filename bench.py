@@ -716,8 +716,9 @@ def run_stability(args):
     the largest lid velocity a 64^3 cavity sustains for 50,000 steps, for
     n = 0.8, 1, 1.5, several tau_p and several sets of the rates omega_9..18,
     by bisection with all open cases of a round in one batch.  With
-    --stability-confirm the FP64 form re-runs each bracket of the unit-rate
-    set at tau_p = 0.51 (the stable and the unstable end)."""
+    --stability-confirm the FP64 form re-runs each bracket of one rate set
+    (--stability-confirm-set, default the unit rates) at tau_p = 0.51 (the
+    stable and the unstable end)."""
     import torch  # noqa: F401  (CUDA context on the chosen device)
     from paper_1908_05396_gb300 import build
     build.build()
@@ -736,7 +737,7 @@ def run_stability(args):
                       "u_unstable": hi} for c, (lo, hi) in zip(cases, res)]}
     if args.stability_confirm:
         sel = [(c, r) for c, r in zip(cases, res)
-               if c.label == "unit" and c.tau_p == 0.51 and r[1] is not None]
+               if c.label == args.stability_confirm_set and c.tau_p == 0.51 and r[1] is not None]
         pairs = [(c, u) for c, (lo, hi) in sel for u in (lo, hi) if u > 0.0]
         t0 = time.perf_counter()
         ok = st.batch_runner(args.stability_L, args.stability_steps, "f64")(
@@ -871,7 +872,8 @@ def main():
     ap.add_argument("--stability-rounds", type=int, default=8)
     ap.add_argument("--stability-dtype", default="f32", choices=["f64", "f32"])
     ap.add_argument("--stability-confirm", action="store_true",
-                    help="re-run the unit-rate brackets at tau_p = 0.51 in FP64")
+                    help="re-run the brackets at tau_p = 0.51 of one rate set in FP64")
+    ap.add_argument("--stability-confirm-set", default="unit", choices=list(STABILITY_RATES))
     ap.add_argument("--oracle-one-core", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_one_core:
