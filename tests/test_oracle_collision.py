@@ -154,6 +154,40 @@ def test_unit_rates_reach_attractors(oracle):
         np.testing.assert_allclose(r2["ft"], ft, atol=2e-16)
 
 
+@pytest.mark.parametrize("seed", SEEDS)
+def test_forced_unit_rates_source_moments(oracle, seed):
+    # Reading [c7]: half of the source S_a is added before and half after the
+    # collision, and the moments of S are 0, F and u*F + Fu* (u* the
+    # half-force velocity).  With every rate 1 the collision takes the second
+    # central moments about u* to c_s^2 rho delta_ij (Eq.
+    # discretecentralmomentattractors), so after the second half of the
+    # source the raw second moments are fixed in closed form:
+    #   sum_a ft_a e_ai e_aj = rho (delta_ij / 3 + u*_i u*_j)
+    #                          + (u*_i F_j + F_i u*_j) / 2.
+    # A wrong sign or a dropped term in the second-order part of S, or S
+    # evaluated at j/rho instead of u*, moves the right-hand side by at least
+    # |u||F|/2 or |F|^2/4 (>= 1e-6 here), far above round-off.
+    rng = np.random.default_rng(700 + seed)
+    e = oracle.velocities().astype(float)
+    for _ in range(20):
+        f = _random_state(oracle, rng)
+        F = rng.uniform(-1e-2, 1e-2, 3)
+        rho = f.sum()
+        j = f @ e
+        us = (j + 0.5 * F) / rho
+        p = oracle.Params(K=rho / 6.0, n=1.0, F=tuple(F))
+        r = oracle.collide(p, f)
+        assert abs(r["omega_nu"] - 1.0) < 1e-15
+        np.testing.assert_allclose(r["u"], us, rtol=0, atol=1e-16)
+        ft = r["ft"]
+        assert abs(ft.sum() - rho) <= 1e-15 * rho
+        np.testing.assert_allclose(ft @ e, j + F, rtol=0, atol=1e-16)
+        second = np.einsum("a,ai,aj->ij", ft, e, e)
+        expect = rho * (np.eye(3) / 3 + np.outer(us, us)) + 0.5 * (np.outer(us, F)
+                                                                  + np.outer(F, us))
+        np.testing.assert_allclose(second, expect, rtol=0, atol=2e-15)
+
+
 def test_newtonian_rate_closed_form(oracle):
     rng = np.random.default_rng(400)
     for _ in range(50):
