@@ -223,15 +223,20 @@ def run_oracle_one_core():
     return 0
 
 
-REF_SLAB = 8   # z-planes of each cavity per reference step (same per-node work)
+def ref_slab(cores: int) -> int:
+    """z-planes of each cavity per reference step: one plane per host core
+    (the oracle's OpenMP loop runs over z-planes, so fewer planes would leave
+    cores idle), at least 16 and at most the whole 128^3 cavity."""
+    return min(L_BENCH, max(16, cores))
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    oracle, lats = _oracle_lattices(nz=REF_SLAB)
     cores = int(os.environ.get("OMP_NUM_THREADS", "0")) or (os.cpu_count() or 1)
+    slab = ref_slab(cores)
+    oracle, lats = _oracle_lattices(nz=slab)
     for _ in range(args.warmup):
         for lt in lats:
             lt[1] = oracle.run(lt[0], lt[1], 1)
@@ -250,8 +255,9 @@ def run_reference(args):
         "config": {"workload": "lid-driven cubic cavity 128^3 x3 (Re=100, n=0.5/1.0/1.5, U=0.05)",
                    "storage": "f64", "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} oracle steps of a 128x128x{REF_SLAB} slab of "
-                                   "each of the three cavities (walls on all faces, lid +y)"},
+                         "sample": f"{args.steps} oracle steps of a 128x128x{slab} slab of "
+                                   "each of the three cavities (walls on all faces, lid +y; "
+                                   "one z-plane per core)"},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))

@@ -81,7 +81,8 @@ typedef enum { CLBM_F64 = 0, CLBM_F32 = 1, CLBM_F16S = 2, CLBM_F16R = 3 } clbm_d
 typedef enum { CLBM_PERIODIC = 0, CLBM_WALL = 1, CLBM_LID = 2 } clbm_bc;
 
 typedef struct {
-  int nx, ny, nz;      /* lattice nodes per axis, each >= 1 */
+  int nx, ny, nz;      /* lattice nodes per axis, each >= 1; ny, nz <= 65535
+                        * (the launch grid has one row per y row and z plane) */
   int face[6];         /* clbm_bc of faces -x, +x, -y, +y, -z, +z */
   double rho0;         /* reference density (rest state, lid); 0 -> 1 */
   double nu_min;       /* kinematic-viscosity clamp; 0 -> 5e-4 */
@@ -404,7 +405,10 @@ int clbm_collide_nodes(clbm_dtype dtype, double K, double n,
  * device looks up the array's device address (cudaGetSymbolAddress) with that
  * device current; make that first call before any stream capture.
  * Queues two kernels and returns without synchronising.
- * Errors: CLBM_ERR_ARG, CLBM_ERR_CUDA (text via clbm_last_error(NULL)). */
+ * Errors: CLBM_ERR_ARG (bad sizes or parameters, checked as for
+ * clbm_create()), CLBM_ERR_UNSUPPORTED (dtype CLBM_F16R), CLBM_ERR_CUDA (a
+ * failed launch, or a first call made inside a stream capture); the text is
+ * in clbm_last_error(NULL). */
 int clbm_step_noalloc(const clbm_domain* d, double K, double n, const double U_lid[3],
                       const double body_force[3], clbm_dtype dtype, const void* src,
                       void* dst, void* u_prev, double* stats);

@@ -20,6 +20,7 @@
 #include "../../include/clbm.h"
 #include "ctx.h"
 #include "launch.h"
+#include "validate.h"
 
 using namespace clbm;
 
@@ -123,32 +124,6 @@ int set_device(clbm_ctx* h) {
 
 bool bad(const clbm_ctx* h) { return h == nullptr || h->buf[0] == nullptr; }
 
-void fill_params(PhysParams& P, double K, double n, const double* F, double rho0,
-                 double nu_min, double nu_max, clbm_dtype dtype) {
-  P.rho0 = rho0;
-  for (int a = 0; a < 3; ++a) P.F[a] = F ? F[a] : 0.0;
-  P.has_force = (P.F[0] != 0.0 || P.F[1] != 0.0 || P.F[2] != 0.0) ? 1 : 0;
-  P.K = K;
-  P.logK3 = std::log(3.0 * K);
-  P.n = n;
-  P.newtonian = (n == 1.0) ? 1 : 0;
-  P.nu_min = nu_min;
-  P.nu_max = nu_max;
-  P.ylo = std::log(3.0 * nu_min);
-  P.yhi = std::log(3.0 * nu_max);
-  P.inv_scale = (dtype == CLBM_F16S || dtype == CLBM_F16R) ? 1.0 / F16_SCALE : 1.0;
-}
-
-int check_phys(double K, double n, double nu_min, double nu_max, std::string& why) {
-  if (!(K > 0.0) || !std::isfinite(K)) { why = "K must be finite and > 0"; return 0; }
-  if (!(n > 0.0 && n <= 3.0)) { why = "n must lie in (0, 3]"; return 0; }
-  if (!(nu_min > 0.0 && nu_max > nu_min) || !std::isfinite(nu_max)) {
-    why = "need 0 < nu_min < nu_max < inf";
-    return 0;
-  }
-  return 1;
-}
-
 }  // namespace
 
 namespace clbm {
@@ -165,8 +140,9 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
     return fail(nullptr, CLBM_ERR_ARG, "unknown dtype");
   if (d->in_place && dtype == CLBM_F16R)
     return fail(nullptr, CLBM_ERR_UNSUPPORTED, "in-place streaming takes FP64, FP32 or F16S storage");
-  if (d->nx < 1 || d->ny < 1 || d->nz < 1)
-    return fail(nullptr, CLBM_ERR_ARG, "lattice dimensions must be >= 1");
+  std::string why;
+  double U[3];
+  if (!check_domain(d, U_lid, U, why)) return fail(nullptr, CLBM_ERR_ARG, why);
   // The kernels index one direction's array (padded rows, 128-byte pitch)
   // with 32-bit integers, neighbours included: keep it well below 2^31.
   {
@@ -177,34 +153,10 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
       return fail(nullptr, CLBM_ERR_ARG,
                   "lattice too large: at most 2^31 - 2^24 padded nodes (32-bit indexing)");
   }
-  bool has_lid = false;
-  for (int f = 0; f < 6; ++f) {
-    if (d->face[f] < CLBM_PERIODIC || d->face[f] > CLBM_LID)
-      return fail(nullptr, CLBM_ERR_ARG, "unknown face kind");
-    has_lid = has_lid || d->face[f] == CLBM_LID;
-  }
-  for (int a = 0; a < 3; ++a)
-    if ((d->face[2 * a] == CLBM_PERIODIC) != (d->face[2 * a + 1] == CLBM_PERIODIC))
-      return fail(nullptr, CLBM_ERR_ARG, "a periodic face needs a periodic opposite face");
-  double U[3] = {0, 0, 0};
-  if (U_lid)
-    for (int a = 0; a < 3; ++a) U[a] = U_lid[a];
-  if (has_lid) {
-    if (!U_lid) return fail(nullptr, CLBM_ERR_ARG, "LID face without U_lid");
-    const double mag = std::sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
-    if (!(mag < 0.3)) return fail(nullptr, CLBM_ERR_ARG, "|U_lid| must be < 0.3");
-    for (int f = 0; f < 6; ++f)
-      if (d->face[f] == CLBM_LID && U[f / 2] != 0.0)
-        return fail(nullptr, CLBM_ERR_ARG, "U_lid must be tangential to every LID face");
-  }
-  const double rho0 = d->rho0 > 0.0 ? d->rho0 : 1.0;
-  const double nu_min = d->nu_min > 0.0 ? d->nu_min : 5e-4;
-  const double nu_max = d->nu_max > 0.0 ? d->nu_max : 10.0;
-  std::string why;
+  double rho0, nu_min, nu_max;
+  domain_defaults(d, &rho0, &nu_min, &nu_max);
   if (!check_phys(K, n, nu_min, nu_max, why)) return fail(nullptr, CLBM_ERR_ARG, why);
-  if (body_force)
-    for (int a = 0; a < 3; ++a)
-      if (!std::isfinite(body_force[a])) return fail(nullptr, CLBM_ERR_ARG, "non-finite force");
+  if (!check_force(body_force, why)) return fail(nullptr, CLBM_ERR_ARG, why);
 
   clbm_ctx* h = new (std::nothrow) clbm_ctx();
   if (!h) return fail(nullptr, CLBM_ERR_OOM, "host allocation failed");

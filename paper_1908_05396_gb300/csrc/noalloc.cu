@@ -17,6 +17,7 @@
 
 #include "../../include/clbm.h"
 #include "kernels.cuh"
+#include "validate.h"
 
 namespace clbm {
 namespace {
@@ -168,38 +169,17 @@ extern "C" int clbm_step_noalloc(const clbm_domain* d, double K, double n, const
   if (!d || !src || !dst || !u_prev || !stats)
     return noalloc_fail(CLBM_ERR_ARG, "null domain or buffer");
   if (src == dst) return noalloc_fail(CLBM_ERR_ARG, "src and dst must be different buffers");
+  if (dtype == CLBM_F16R)
+    return noalloc_fail(CLBM_ERR_UNSUPPORTED, "the F16R form is not available here");
   if (dtype != CLBM_F64 && dtype != CLBM_F32 && dtype != CLBM_F16S)
-    return noalloc_fail(dtype == 3 ? CLBM_ERR_UNSUPPORTED : CLBM_ERR_ARG,
-                        dtype == 3 ? "the F16R form is not available here" : "unknown dtype");
-  if (d->nx < 1 || d->ny < 1 || d->nz < 1)
-    return noalloc_fail(CLBM_ERR_ARG, "lattice dimensions must be >= 1");
-  bool has_lid = false;
-  for (int f = 0; f < 6; ++f) {
-    if (d->face[f] < CLBM_PERIODIC || d->face[f] > CLBM_LID)
-      return noalloc_fail(CLBM_ERR_ARG, "unknown face kind");
-    has_lid = has_lid || d->face[f] == CLBM_LID;
-  }
-  for (int a = 0; a < 3; ++a)
-    if ((d->face[2 * a] == CLBM_PERIODIC) != (d->face[2 * a + 1] == CLBM_PERIODIC))
-      return noalloc_fail(CLBM_ERR_ARG, "a periodic face needs a periodic opposite face");
-  double U[3] = {0, 0, 0};
-  if (U_lid)
-    for (int a = 0; a < 3; ++a) U[a] = U_lid[a];
-  if (has_lid) {
-    if (!U_lid) return noalloc_fail(CLBM_ERR_ARG, "LID face without U_lid");
-    const double mag = std::sqrt(U[0] * U[0] + U[1] * U[1] + U[2] * U[2]);
-    if (!(mag < 0.3)) return noalloc_fail(CLBM_ERR_ARG, "|U_lid| must be < 0.3");
-    for (int f = 0; f < 6; ++f)
-      if (d->face[f] == CLBM_LID && U[f / 2] != 0.0)
-        return noalloc_fail(CLBM_ERR_ARG, "U_lid must be tangential to every LID face");
-  }
-  const double rho0 = d->rho0 > 0.0 ? d->rho0 : 1.0;
-  const double nu_min = d->nu_min > 0.0 ? d->nu_min : 5e-4;
-  const double nu_max = d->nu_max > 0.0 ? d->nu_max : 10.0;
-  if (!(K > 0.0) || !std::isfinite(K)) return noalloc_fail(CLBM_ERR_ARG, "K must be finite and > 0");
-  if (!(n > 0.0 && n <= 3.0)) return noalloc_fail(CLBM_ERR_ARG, "n must lie in (0, 3]");
-  if (!(nu_min > 0.0 && nu_max > nu_min) || !std::isfinite(nu_max))
-    return noalloc_fail(CLBM_ERR_ARG, "need 0 < nu_min < nu_max < inf");
+    return noalloc_fail(CLBM_ERR_ARG, "unknown dtype");
+  std::string why;
+  double U[3];
+  if (!check_domain(d, U_lid, U, why)) return noalloc_fail(CLBM_ERR_ARG, why.c_str());
+  double rho0, nu_min, nu_max;
+  domain_defaults(d, &rho0, &nu_min, &nu_max);
+  if (!check_phys(K, n, nu_min, nu_max, why)) return noalloc_fail(CLBM_ERR_ARG, why.c_str());
+  if (!check_force(body_force, why)) return noalloc_fail(CLBM_ERR_ARG, why.c_str());
 
   // Dense layout: pop[q][z][y][x] with no padding, u_prev[3][z][y][x].
   Geom g{};
@@ -214,19 +194,7 @@ extern "C" int clbm_step_noalloc(const clbm_domain* d, double K, double n, const
   for (int a = 0; a < 3; ++a) g.U[a] = U[a];
   g.rho0 = rho0;
   PhysParams P{};
-  P.rho0 = rho0;
-  for (int a = 0; a < 3; ++a) P.F[a] = body_force ? body_force[a] : 0.0;
-  P.has_force = (P.F[0] != 0.0 || P.F[1] != 0.0 || P.F[2] != 0.0) ? 1 : 0;
-  P.K = K;
-  P.logK3 = std::log(3.0 * K);
-  P.n = n;
-  P.newtonian = (n == 1.0) ? 1 : 0;
-  P.nu_min = nu_min;
-  P.nu_max = nu_max;
-  P.ylo = std::log(3.0 * nu_min);
-  P.yhi = std::log(3.0 * nu_max);
-  P.inv_scale = dtype == CLBM_F16S ? 1.0 / F16_SCALE : 1.0;
-
+  fill_params(P, K, n, body_force, rho0, nu_min, nu_max, dtype);
   const dim3 block(32, 4, 1);
   const dim3 grid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz);
   const int64_t nblocks = int64_t(grid.x) * grid.y * grid.z;
@@ -241,9 +209,20 @@ extern "C" int clbm_step_noalloc(const clbm_domain* d, double K, double n, const
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   double* partials = nullptr;
-  if (e == cudaSuccess) e = scratch_address(dev, &partials);
-  if (e != cudaSuccess) return noalloc_fail(CLBM_ERR_CUDA, cudaGetErrorString(e));
   cudaStream_t st = static_cast<cudaStream_t>(d->stream);
+  if (e == cudaSuccess) e = scratch_address(dev, &partials);
+  if (e != cudaSuccess) {
+    // The first call on a device looks the scratch address up, which a
+    // stream capture in progress does not allow.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+      std::string m = std::string(cudaGetErrorString(e)) +
+                      ": the first clbm_step_noalloc call on a device must come before any "
+                      "stream capture";
+      return noalloc_fail(CLBM_ERR_CUDA, m.c_str());
+    }
+    return noalloc_fail(CLBM_ERR_CUDA, cudaGetErrorString(e));
+  }
   switch (dtype) {
     case CLBM_F64:
       e = launch_noalloc<double, double>(src, dst, g, P, u_prev, partials, stats, grid, block, st);

@@ -64,6 +64,8 @@ def _create(clbm, **kw):
     (dict(face=(0, 0, 5, 1, 0, 0)), "face kind"),
     (dict(dims=(1400, 1400, 1400), dtype=2), "too large"),   # fits HBM in FP16, not int32
     (dict(dims=(1290, 1290, 1290), dtype=1), "too large"),
+    (dict(dims=(1, 1, 65536)), "65535"),      # one launch grid row per z plane
+    (dict(dims=(1, 65536, 1)), "65535"),
 ])
 def test_create_rejects_bad_arguments(clbm, kw, frag):
     rc, msg = _create(clbm, **kw)
@@ -94,3 +96,18 @@ def test_set_allocator_needs_both_functions(clbm):
     assert L.clbm_set_allocator(null_a, null_f, None) == clbm.OK
     with pytest.raises(ValueError):
         clbm.set_allocator(lambda n, d, s: 0, None)
+
+
+@pytest.mark.parametrize("dims,dtype,code,frag", [
+    ((1, 1, 65536), "f32", "ERR_ARG", "65535"),
+    ((0, 4, 4), "f32", "ERR_ARG", "dimensions"),
+    ((8, 8, 8), "f16r", "ERR_UNSUPPORTED", "F16R"),
+    ((8, 8, 8), 9, "ERR_ARG", "dtype"),
+])
+def test_noalloc_rejects_bad_arguments(clbm, dims, dtype, code, frag):
+    # Argument checks of clbm_step_noalloc run before any device access; the
+    # buffer addresses are never dereferenced here.
+    rc = clbm.step_noalloc(*dims, face=(0,) * 6, K=0.1, n=1.0, U_lid=None, body_force=None,
+                           dtype=dtype, src=4096, dst=8192, u_prev=12288, stats=16384)
+    assert rc == getattr(clbm, code)
+    assert frag in clbm.last_error()

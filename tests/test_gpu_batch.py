@@ -195,3 +195,34 @@ def test_step_refused_while_batched(clbm):
             lat.step(1)
     lat.step(1)                      # the batch is gone: stepping alone works again
     lat.close()
+
+
+def _oracle_params(oracle, prob):
+    return oracle.Params(nx=prob.nx, ny=prob.ny, nz=prob.nz, face=prob.face, K=prob.K, n=prob.n,
+                         U=prob.U_lid, F=prob.body_force)
+
+
+@pytest.mark.parametrize("mode", ["persistent", "per_lattice"])
+def test_batch_members_vs_oracle(clbm, oracle, mode):
+    # Every member of an FP64 batch (cavities, a forced channel and a forced
+    # periodic box) against the oracle directly, not only through the lone
+    # lattice: the FP64 bar, max|du| <= 1e-10 of the member's velocity scale
+    # and the populations to 1e-12.
+    probs = _mix(4)
+    steps = 300
+    lats = [clbm.Lattice(**p.kwargs(), dtype="f64", check_interval=50) for p in probs]
+    with clbm.Batch("f64", capacity=8, check_interval=50) as b:
+        _set_mode(b, mode)
+        for lt in lats:
+            b.add(lt)
+        b.step(steps)
+        got = [(lt.get_state(), lt.fields()[1]) for lt in lats]
+    for lt, p, (f, u) in zip(lats, probs, got):
+        op = _oracle_params(oracle, p)
+        f_ref = oracle.run(op, oracle.rest_state(op), steps)
+        _, u_ref, _ = oracle.fields(op, f_ref)
+        scale = np.abs(u_ref).max()
+        assert scale > 1e-6
+        assert np.abs(u - u_ref).max() <= 1e-10 * scale
+        assert np.abs(f - f_ref).max() <= 1e-12
+        lt.close()

@@ -119,9 +119,13 @@ def test_rest_states_agree(clbm, oracle):
     assert np.array_equal(f, oracle.rest_state(_oracle_params(oracle, prob)))
 
 
-@pytest.mark.parametrize("n", [0.5, 1.0, 1.5])
-def test_cavity_f64_1000_steps(clbm, oracle, n):
-    prob = wl.cavity(32, 100.0, n)
+@pytest.mark.parametrize("L,n", [(32, 0.5), (32, 1.0), (32, 1.5), (64, 0.5), (64, 1.0),
+                                 (64, 1.5), (128, 0.5)])
+def test_cavity_f64_1000_steps(clbm, oracle, L, n):
+    # The FP64 bar at the cavity sizes of the parity list (32^3, 64^3 and
+    # the 128^3 benchmark lattice), Re 100, 1000 steps from rest.  The
+    # oracle takes about 20 s per 64^3 case and 3 min for 128^3 on 16 cores.
+    prob = wl.cavity(L, 100.0, n)
     p = _oracle_params(oracle, prob)
     with _lattice(clbm, prob, "f64") as lat:
         lat.step(1000)
@@ -377,6 +381,54 @@ def test_mass_conserved_and_residual_defined(clbm):
         assert 0 < R < 1 and rc == 0
         lat.step(400)
         assert abs(lat.mass() - prob.N) <= 1e-12 * prob.N
+
+
+@pytest.fixture(scope="module")
+def mixed_check_reference(oracle):
+    # The oracle's velocity fields of the ragged mixed lattice at the two
+    # states whose collisions are check steps 1 and 2 of a check interval of
+    # 50: a check step computes u from the state after 49 (99) steps.
+    p = _oracle_params(oracle, _MIXED)
+    r = wl.noise((19, 9, 17, 33), seed=7, amp=0.05)
+    f = oracle.rest_state(p) * (1 + r)
+    f49 = oracle.run(p, f, 49)
+    f99 = oracle.run(p, f49, 50)
+    _, u49, _ = oracle.fields(p, f49)
+    _, u99, _ = oracle.fields(p, f99)
+    return r, u49, u99, oracle.mass(p, f99)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_residual_and_mass_vs_oracle(clbm, oracle, mixed_check_reference, dtype):
+    # Reading c11: R = ||u(t) - u(t - D)|| / (D ||u(t)||) over all nodes, in
+    # FP64 sums, at every D-th step.  The device reduction is compared with
+    # the oracle's definition applied (a) to the GPU's own velocity fields at
+    # the two check states and (b) to the oracle's fields of the same run; the
+    # check step's mass sum with the oracle's sum of the populations.
+    r, u49_ref, u99_ref, m_ref = mixed_check_reference
+    D = 50
+    with _lattice(clbm, _MIXED, dtype, check_interval=D) as lat:
+        rest = lat.get_state()
+        lat.set_state(rest * (1 + r))
+        lat.step(D - 1)
+        _, u49, _ = lat.fields()
+        lat.step(D)
+        _, u99, _ = lat.fields()
+        lat.step(1)
+        R, rc = lat.residual()
+        assert rc == 0
+        m = lat.mass()
+    R_own = oracle.residual(u99, u49, D)
+    R_ref = oracle.residual(u99_ref, u49_ref, D)
+    assert R_ref > 1e-5          # a genuine transient: the fields differ
+    if dtype == "f64":
+        assert abs(R - R_own) <= 1e-12 * R_own
+        assert abs(R - R_ref) <= 1e-9 * R_ref
+        assert abs(m - m_ref) <= 1e-12 * m_ref
+    else:
+        assert abs(R - R_own) <= 1e-5 * R_own
+        assert abs(R - R_ref) <= 1e-3 * R_ref
+        assert abs(m - m_ref) <= 1e-6 * m_ref
 
 
 def test_divergence_is_reported(clbm):

@@ -95,3 +95,27 @@ def test_destroy_cancels_unfinished(clbm):
     info = srv.info()
     assert info["active"] == 1 and info["queued"] == 2
     srv.close()
+
+
+def test_served_results_vs_oracle(clbm, oracle):
+    # FP64 requests served together (two slots for three requests, so one
+    # joins while the others run), each stopped by its step cap, against the
+    # oracle run for the same number of steps: max|du| <= 1e-10 of the
+    # request's velocity scale.
+    probs = _requests()[:2] + [_requests()[4]]
+    caps = [700, 900, 500]
+    with clbm.Server("f64", hbm_budget_bytes=4e9, max_active=2, check_interval=50) as srv:
+        ids = [srv.submit(**p.kwargs(), tol=0.0, max_steps=c, keep_fields=True)
+               for p, c in zip(probs, caps)]
+        res = [srv.wait(rid, timeout=120) for rid in ids]
+        fields = [srv.fields(rid) for rid in ids]
+    for p, c, r, (rho, u, _) in zip(probs, caps, res, fields):
+        assert r["status"] == 1 and r["steps"] == c          # the step cap
+        op = oracle.Params(nx=p.nx, ny=p.ny, nz=p.nz, face=p.face, K=p.K, n=p.n, U=p.U_lid,
+                           F=p.body_force)
+        f_ref = oracle.run(op, oracle.rest_state(op), c)
+        rho_ref, u_ref, _ = oracle.fields(op, f_ref)
+        scale = np.abs(u_ref).max()
+        assert scale > 1e-6
+        assert np.abs(u - u_ref).max() <= 1e-10 * scale
+        assert np.abs(rho - rho_ref).max() <= 1e-12
