@@ -372,6 +372,16 @@ int clbm_collide_nodes(clbm_dtype dtype, double K, double n,
                        double nu_max, const double* f_in, double* f_out,
                        double* rho, double* u, double* gamma_dot, int64_t M);
 
+/* Fused multiply-add throughput of the current device, in FLOP/s (two per
+ * FMA), for dtype CLBM_F64 or CLBM_F32: a measurement utility with no
+ * counterpart in the paper.  It gives the arithmetic ceiling of a step form
+ * bound by its arithmetic pipe instead of HBM (the FP64 form on GB300): one
+ * grid of 8 blocks of 256 threads per SM, eight independent FMA chains per
+ * thread, timed with CUDA events on the legacy default stream (about 0.1 s,
+ * after a shorter warm-up launch).  Synchronous; allocates no device memory.
+ * Errors: CLBM_ERR_ARG (other dtype, NULL out), CLBM_ERR_CUDA. */
+int clbm_probe_fma_rate(clbm_dtype dtype, double* flops_per_s);
+
 /* One check step between caller-owned device buffers, with no device memory
  * allocated by the library.  The paper has no counterpart: this entry point
  * exists for callers that cannot call cudaMalloc while they step -- a host

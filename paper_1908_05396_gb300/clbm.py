@@ -84,7 +84,8 @@ def lib():
             L.clbm_set_launch.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             L.clbm_set_rates.argtypes = [_H, _D]
             L.clbm_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, ctypes.c_void_p]
-            for name in ("clbm_autotune", "clbm_set_launch", "clbm_set_rates", "clbm_set_allocator",
+            L.clbm_probe_fma_rate.argtypes = [ctypes.c_int, _D]
+            for name in ("clbm_probe_fma_rate", "clbm_autotune", "clbm_set_launch", "clbm_set_rates", "clbm_set_allocator",
                          "clbm_create", "clbm_step", "clbm_fields", "clbm_fields_device",
                          "clbm_residual", "clbm_mass", "clbm_get_state", "clbm_set_state",
                          "clbm_steps_done", "clbm_sync", "clbm_destroy", "clbm_collide_nodes"):
@@ -326,6 +327,15 @@ def step_noalloc(nx, ny, nz, face, K, n, U_lid, body_force, dtype, src, dst, u_p
     return L.clbm_step_noalloc(ctypes.byref(d), float(K), float(n), _vec3(U_lid), _vec3(body_force),
                                code, ctypes.c_void_p(src), ctypes.c_void_p(dst),
                                ctypes.c_void_p(u_prev), ctypes.c_void_p(stats))
+
+
+def probe_fma_rate(dtype="f64") -> float:
+    """FMA throughput of the current device in FLOP/s (``clbm_probe_fma_rate``)."""
+    L = lib()
+    out = ctypes.c_double(0.0)
+    code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    _check(L.clbm_probe_fma_rate(code, ctypes.byref(out)))
+    return out.value
 
 
 def last_error() -> str:
