@@ -131,32 +131,47 @@ class Clocks:
 
 
 STEP_KERNEL_SOURCES = ("d3q19.cuh", "v2.cuh", "collide.cuh", "launch.h", "kernels.cuh",
-                       "tma_step.cuh", "step_f32.cu")
+                       "tma_step.cuh")
+# translation unit of each storage form's step kernel
+STEP_TU = {"f64": "step_f64.cu", "f32": "step_f32.cu", "f16s": "step_f16.cu"}
 
 
-def kernel_source_hash() -> str:
-    """Hash of the sources that define the FP32 step kernel (its headers and
+def kernel_source_hash(form: str = "f32") -> str:
+    """Hash of the sources that define one form's step kernel (its headers and
     translation unit), so that changes elsewhere keep a capture valid."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1908_05396_gb300", "csrc")
     h = hashlib.sha256()
-    for fn in STEP_KERNEL_SOURCES:
+    for fn in STEP_KERNEL_SOURCES + (STEP_TU[form],):
         h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()[:16]
 
 
-def _traffic_note(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the
-    current kernel sources (else null)."""
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
+def _profile_note(fname: str, kernel: str, form: str):
+    """The numbers after the kernel name and source hash in a committed ncu
+    summary table under profiles/, if they were taken on the current kernel
+    sources (else None)."""
+    path = os.path.join(ROOT, "profiles", fname)
     if not os.path.exists(path):
         return None
-    digest = kernel_source_hash()
+    digest = kernel_source_hash(form)
     for line in open(path):
         parts = line.split()
         if len(parts) >= 3 and parts[0] == kernel and parts[1] == digest:
-            return float(parts[2])
+            return [float(x) for x in parts[2:]]
     return None
+
+
+def _traffic_note(kernel: str, form: str = "f32"):
+    """DRAM bytes per launch (read + write) from the committed ncu summary."""
+    v = _profile_note("traffic.txt", kernel, form)
+    return v[0] if v else None
+
+
+def _fp64_ops_note(kernel: str):
+    """FP64 instructions per node update (DADD, DFMA, DMUL) of the FP64 step
+    kernel from the committed ncu summary."""
+    return _profile_note("fp64_ops.txt", kernel, "f64")
 
 
 def _oracle_lattices(nz: int | None = None):
@@ -362,6 +377,29 @@ def run_ours(args):
     forms[head] = {"MLUPS": value / ws, "GB/s": achieved, "frac_of_hbm": achieved / peak,
                    "steps": args.steps, "bytes_per_update": bpn,
                    "launch": [(t["block"], t["npt"]) for t in tuned]}
+    # The FP64 form is bound by the FP64 pipe, not HBM: its roofline is the
+    # FP64 instruction rate (one DADD, DMUL or DFMA per slot), measured live
+    # by the FMA probe, against the FP64 instructions per update counted by
+    # ncu on the current kernel sources.
+    if "f64" in forms:
+        rate = clbm.probe_fma_rate("f64")
+        kern64 = "step_kernel<double,double,false,false,false>"
+        ops = _fp64_ops_note(kern64)
+        alu = {"bound": "alu", "unit": "FP64 instructions/s", "peak": rate / 2.0,
+               "peak_kind": "measured (FMA probe: two FLOP per DFMA)", "kernel": kern64,
+               "probe_tflops": rate / 1e12}
+        if ops:
+            per_node = sum(ops)
+            alu.update({"fp64_instructions_per_update": per_node,
+                        "achieved": per_node * forms["f64"]["MLUPS"] * 1e6,
+                        "flops_per_update": ops[0] + 2.0 * ops[1] + ops[2]})
+            alu["frac"] = alu["achieved"] / alu["peak"]
+            alu["tflops"] = alu["flops_per_update"] * forms["f64"]["MLUPS"] * 1e6 / 1e12
+        forms["f64"]["alu_roofline"] = alu
+    summary = {k: {"MLUPS": round(v["MLUPS"], 1), "frac_of_hbm": round(v["frac_of_hbm"], 4)}
+               for k, v in forms.items()}
+    if "f64" in forms and "frac" in forms["f64"]["alu_roofline"]:
+        summary["f64"]["frac_of_fp64_pipe"] = round(forms["f64"]["alu_roofline"]["frac"], 4)
 
     # ---- end to end through the C ABI with host buffers ------------------------
     # The same three-cavity job from pinned host states: per lattice, create,
@@ -422,7 +460,8 @@ def run_ours(args):
                          "peak_kind": peak_kind, "kernel": kern,
                          "algorithmic_bytes_per_launch": bpn * N,
                          "duration": "timed region / launches, three lattices on three streams "
-                                     "(launches overlap)"},
+                                     "(launches overlap)",
+                         "forms": summary},
             "forms": forms,
             "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,

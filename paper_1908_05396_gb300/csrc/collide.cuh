@@ -27,9 +27,12 @@ struct CollideConst {
   R F[3];        // body force
   R K3;          // 3 K (K = mu_p, consistency coefficient, Eq. 5)
   R logK3;       // log(3 K)
+  R log2K3;      // log2(3 K)
   R n;           // power-law index
+  R rn;          // 1 / n
   R ehalf;       // (n - 1) / 2
   R ylo, yhi;    // log(3 nu_min), log(3 nu_max): clamp of y = log(1/w - 1/2)
+  R ylo2, yhi2;  // the same clamp in base 2
   R nu_min, nu_max;
   int newtonian; // n == 1: omega_nu has a closed form
   int has_force;
@@ -49,12 +52,23 @@ struct NodeOut {
   R rho, ux, uy, uz, gamma_dot;
 };
 
-template <typename R> __device__ __forceinline__ R rlog(R x);
-template <> __device__ __forceinline__ float rlog<float>(float x) { return __logf(x); }
-template <> __device__ __forceinline__ double rlog<double>(double x) { return log(x); }
-template <typename R> __device__ __forceinline__ R rexp(R x);
-template <> __device__ __forceinline__ float rexp<float>(float x) { return __expf(x); }
-template <> __device__ __forceinline__ double rexp<double>(double x) { return exp(x); }
+// Base-2 logarithm and power of two on the special-function unit (PTX
+// lg2.approx / ex2.approx, about 22 correct bits): the FP32 solve for
+// omega_nu works in base 2, so no conversion factor is spent on either.
+__device__ __forceinline__ float lg2f(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2f(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+template <typename R> __device__ __forceinline__ R rlg2(R x);
+template <> __device__ __forceinline__ float rlg2<float>(float x) { return lg2f(x); }
+template <typename R> __device__ __forceinline__ R rex2(R x);
+template <> __device__ __forceinline__ float rex2<float>(float x) { return ex2f(x); }
 template <typename R> __device__ __forceinline__ R rdiv(R a, R b);
 template <> __device__ __forceinline__ float rdiv<float>(float a, float b) { return __fdividef(a, b); }
 template <> __device__ __forceinline__ double rdiv<double>(double a, double b) { return a / b; }
@@ -64,8 +78,8 @@ template <typename R> __device__ __forceinline__ R rrcp(R x);
 template <> __device__ __forceinline__ float rrcp<float>(float x) { return __fdividef(1.0f, x); }
 template <> __device__ __forceinline__ double rrcp<double>(double x) { return 1.0 / x; }
 
-template <> __device__ __forceinline__ V2 rlog<V2>(V2 x) { return V2(__logf(x.v.x), __logf(x.v.y)); }
-template <> __device__ __forceinline__ V2 rexp<V2>(V2 x) { return V2(__expf(x.v.x), __expf(x.v.y)); }
+template <> __device__ __forceinline__ V2 rlg2<V2>(V2 x) { return V2(lg2f(x.v.x), lg2f(x.v.y)); }
+template <> __device__ __forceinline__ V2 rex2<V2>(V2 x) { return V2(ex2f(x.v.x), ex2f(x.v.y)); }
 template <> __device__ __forceinline__ V2 rdiv<V2>(V2 a, V2 b) {
   return V2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y));
 }
@@ -78,26 +92,41 @@ template <> __device__ __forceinline__ float tiny<float>() { return 1e-36f; }
 template <> __device__ __forceinline__ double tiny<double>() { return 1e-300; }
 template <> __device__ __forceinline__ V2 tiny<V2>() { return V2(1e-36f); }
 
-// Newton iterations on y = log(1/omega - 1/2) for
-//   G(y) = y - log(3K/rho) - (n-1)/2 log(omega(y)^2 A + B) = 0,
+// Starting point of the solve below.  Without the bulk part B, the unknown
+// z = 1/omega - 1/2 = 3 nu solves z (z + 1/2)^(n-1) = P with
+// log2 P = log2(3K/rho) + (n-1)/2 log2 A, whose two asymptotes are
+// z = P^(1/n) (z >> 1/2) and z = 2^(n-1) P (z << 1/2); they meet at z = 1/2,
+// where log2 P = -n.  The guess takes the asymptote of its side (with A + B
+// for A), which three Newton steps then take to the FP32 rounding level
+// over the workloads' range of n, K and shear rate.
+__device__ __forceinline__ float regime_guess(float lp, float n, float rn) {
+  return lp > -n ? lp * rn : lp + (n - 1.0f);
+}
+__device__ __forceinline__ V2 regime_guess(V2 lp, float n, float rn) {
+  return V2(regime_guess(lp.v.x, n, rn), regime_guess(lp.v.y, n, rn));
+}
+
+// Newton iterations on y = log2(1/omega - 1/2) for
+//   G(y) = y - log2(3K/rho) - (n-1)/2 log2(omega(y)^2 A + B) = 0,
 // i.e. 1/omega - 1/2 = 3 nu with nu = (K/rho) gamma_dot^(n-1) (Eq. 6,
 // Eq. localvarationsrelaxationtimes) and gamma_dot^2 = omega^2 A + B: the
 // omega part of the strain rate of Eq. strainratetensor is traceless, so its
 // invariant (Eq. shearrateexpression) is quadratic in omega.
 // dG/dy = 1 + (n-1) r tau omega with r = omega^2 A / gamma_dot^2 and
-// tau omega in (0, 1), so G is increasing with slope between min(n, 1) and
-// max(n, 1) and has one root; projecting each iterate onto [ylo, yhi] makes
-// the iteration land on the clamp when the root lies beyond it.
+// tau omega in (0, 1) (the base of the logarithm cancels), so G is
+// increasing with slope between min(n, 1) and max(n, 1) and has one root;
+// projecting each iterate onto [ylo, yhi] makes the iteration land on the
+// clamp when the root lies beyond it.
 template <typename R>
-__device__ __forceinline__ R newton_y(R y, R c, R ehalf, R nm1, R A, R B,
-                                      R ylo, R yhi, int iters) {
+__device__ __forceinline__ R newton_y2(R y, R c, R ehalf, R nm1, R A, R B, R ylo, R yhi,
+                                       int iters) {
 #pragma unroll 1
   for (int it = 0; it < iters; ++it) {
-    R tau = rexp<R>(y);
+    R tau = rex2<R>(y);
     R w = rrcp<R>(tau + R(0.5));
     R wwA = w * w * A;
     R g2 = fmax(wwA + B, tiny<R>());
-    R G = y - c - ehalf * rlog<R>(g2);
+    R G = (y - c) - ehalf * rlg2<R>(g2);
     R dG = R(1) + nm1 * rdiv<R>(wwA, g2) * (tau * w);
     y = fmin(fmax(y - rdiv<R>(G, dG), ylo), yhi);
   }
@@ -105,8 +134,8 @@ __device__ __forceinline__ R newton_y(R y, R c, R ehalf, R nm1, R A, R B,
 }
 
 // omega_nu from A and B (see above); writes |gamma_dot| at that omega.
-// FP32 (one node or a pair): four Newton iterations from the guess
-// omega = 2/3 reach the FP32 rounding level.
+// FP32 (one node or a pair): the regime guess and three Newton steps reach
+// the FP32 rounding level.
 template <typename R>
 __device__ __forceinline__ R omega_nu(const CollideConst<float>& C, R rho, R rinv, R A, R B,
                                       R* gd) {
@@ -115,18 +144,27 @@ __device__ __forceinline__ R omega_nu(const CollideConst<float>& C, R rho, R rin
     R nu = fmin(fmax(R(C.K3 * (1.0f / 3.0f)) * rinv, R(C.nu_min)), R(C.nu_max));
     w = rrcp<R>(R(3.0f) * nu + R(0.5f));
   } else {
-    const R c = R(C.logK3) - rlog<R>(rho);
-    R y0 = c + R(C.ehalf) * rlog<R>(fmax(A * R(4.0f / 9.0f) + B, tiny<R>()));
-    y0 = fmin(fmax(y0, R(C.ylo)), R(C.yhi));
-    const R y = newton_y<R>(y0, c, R(C.ehalf), R(C.n - 1.0f), A, B, R(C.ylo), R(C.yhi), 4);
-    w = rrcp<R>(rexp<R>(y) + R(0.5f));
+    const R c = R(C.log2K3) - rlg2<R>(rho);
+    const R lp = c + R(C.ehalf) * rlg2<R>(fmax(A + B, tiny<R>()));
+    R y0 = regime_guess(lp, C.n, C.rn);
+    y0 = fmin(fmax(y0, R(C.ylo2)), R(C.yhi2));
+    const R y = newton_y2<R>(y0, c, R(C.ehalf), R(C.n - 1.0f), A, B, R(C.ylo2), R(C.yhi2), 3);
+    w = rrcp<R>(rex2<R>(y) + R(0.5f));
   }
   *gd = sqrt(fmax(w * w * A + B, R(0.0f)));
   return w;
 }
 
-// FP64: the same four iterations in FP32, then two in FP64, which take the
-// FP32 estimate to the FP64 rounding level (quadratic convergence).
+// FP64: the FP32 solve, then one Halley step in FP64 on the natural-log
+// y = log(1/omega - 1/2).  Halley's step converges cubically, so from the
+// FP32 estimate (relative error ~1e-5) it lands at the FP64 rounding level.
+// With s = tau omega and r as above,
+//   G'  = 1 + (n-1) r s,
+//   G'' = (n-1) [s omega r / 2 - 2 r (1 - r) s^2]
+// (from d(tau omega)/dy = tau omega^2 / 2 and dr/dy = -2 r (1 - r) s), and
+// the step is dy = -2 G G' / (2 G'^2 - G G'').  tau = exp(y) is then carried
+// to the new y by exp(dy) = 1 + dy + dy^2/2 + dy^3/6 (|dy| ~ 1e-5, so the
+// omitted terms lie below 1e-20), or set to 3 nu exactly on a clamp.
 __device__ __forceinline__ double omega_nu(const CollideConst<double>& C, double rho,
                                            double rinv, double A, double B, double* gd) {
   double w;
@@ -134,52 +172,211 @@ __device__ __forceinline__ double omega_nu(const CollideConst<double>& C, double
     double nu = fmin(fmax(C.K3 * (1.0 / 3.0) * rinv, C.nu_min), C.nu_max);
     w = 1.0 / (3.0 * nu + 0.5);
   } else {
-    float cf = float(C.logK3) - __logf(float(rho));
-    float Af = float(A), Bf = float(B);
-    float y0 = cf + float(C.ehalf) * __logf(fmaxf(Af * (4.0f / 9.0f) + Bf, 1e-36f));
-    y0 = fminf(fmaxf(y0, float(C.ylo)), float(C.yhi));
-    float yf = newton_y<float>(y0, cf, float(C.ehalf), float(C.n) - 1.0f, Af, Bf,
-                               float(C.ylo), float(C.yhi), 4);
-    const double c = C.logK3 - log(rho);
-    double y = newton_y<double>(double(yf), c, C.ehalf, C.n - 1.0, A, B, C.ylo, C.yhi, 2);
-    w = 1.0 / (exp(y) + 0.5);
+    const float rf = float(rho), Af = float(A), Bf = float(B);
+    const float cf = float(C.log2K3) - lg2f(rf);
+    const float lp = cf + float(C.ehalf) * lg2f(fmaxf(Af + Bf, 1e-36f));
+    float yf = regime_guess(lp, float(C.n), float(C.rn));
+    yf = fminf(fmaxf(yf, float(C.ylo2)), float(C.yhi2));
+    yf = newton_y2<float>(yf, cf, float(C.ehalf), float(C.n) - 1.0f, Af, Bf, float(C.ylo2),
+                          float(C.yhi2), 3);
+    const double y0 = fmin(fmax(double(yf) * 0.69314718055994530942, C.ylo), C.yhi);
+    const double tau = exp(y0);
+    const double w0 = 1.0 / (tau + 0.5);
+    const double wwA = w0 * w0 * A;
+    const double g2 = fmax(wwA + B, 1e-300);
+    const double nm1 = C.n - 1.0;
+    const double G = (y0 - (C.logK3 - log(rho))) - C.ehalf * log(g2);
+    const double r = wwA / g2;
+    const double sw = tau * w0;
+    const double G1 = 1.0 + nm1 * r * sw;
+    const double G2 = nm1 * (sw * (0.5 * w0) * r - 2.0 * r * (1.0 - r) * sw * sw);
+    const double dy = -2.0 * G * G1 / (2.0 * G1 * G1 - G * G2);
+    const double y1 = y0 + dy;
+    double tau1;
+    if (y1 <= C.ylo) tau1 = 3.0 * C.nu_min;
+    else if (y1 >= C.yhi) tau1 = 3.0 * C.nu_max;
+    else tau1 = tau + tau * (dy * (1.0 + dy * (0.5 + dy * (1.0 / 6.0))));
+    w = 1.0 / (tau1 + 0.5);
   }
   *gd = sqrt(fmax(w * w * A + B, 0.0));
   return w;
 }
 
-// Coefficient of g^_j (j >= 4) in f~_q as the grouped back-transform in
-// collide() forms it; grouping_is_K() checks it against every entry of K.
-constexpr int grouped_coef(int q, int j) {
-  const int x = cx(q), y = cy(q), z = cz(q);
-  const int axes = (x != 0) + (y != 0) + (z != 0);
-  if (axes == 0) return j == 9 ? -30 : j == 16 ? 12 : 0;
-  if (axes == 1) {  // Ca = -11 g9 - 4 g16, then the axis's own terms
-    int c = j == 9 ? -11 : j == 16 ? -4 : 0;
-    if (x) c += (j == 7 || j == 8) ? 1 : j == 17 ? -4 : j == 10 ? -4 * x : 0;
-    if (y) c += j == 7 ? -1 : j == 8 ? 1 : j == 17 ? 2 : j == 18 ? -2 : j == 11 ? -4 * y : 0;
-    if (z) c += j == 8 ? -2 : (j == 17 || j == 18) ? 2 : j == 12 ? -4 * z : 0;
-    return c;
+// ---- pair space -------------------------------------------------------------
+// The collision works on the nine +/- velocity pairs instead of the 19
+// populations.  An axis pair (e, -e) is held as its sum s and difference t;
+// in each coordinate plane the two diagonal pairs P (e_i e_j = +1) and
+// M (e_i e_j = -1) are held as four moments of the plane, e.g. in the xy
+// plane, with sP = d7 + d10, tP = d7 - d10, sM = d9 + d8, tM = d9 - d8,
+//   Dxxyy = sP + sM, Dxy = sP - sM, Dxyy = tP + tM, Dxxy = tP - tM.
+// These 19 values are the rest population, the axis sums and differences and
+// the plane moments: the raw moments of Eq. rawmomentdistributionfunction1
+// are sums of them, and the populations are recovered from them exactly.
+// The post-collision populations are rebuilt from the pair values and g^
+// at the end, so the 19 pre-collision populations need not stay live
+// through the collision.
+template <typename R>
+struct Pairs {
+  R d0;
+  R sAx, tAx, sAy, tAy, sAz, tAz;
+  R Dxxyy, Dxy, Dxyy, Dxxy;  // xy plane: velocities 7, 10 (P) and 9, 8 (M)
+  R Dxxzz, Dxz, Dxzz, Dxxz;  // xz plane: 11, 14 (P) and 13, 12 (M)
+  R Dyyzz, Dyz, Dyzz, Dyyz;  // yz plane: 15, 18 (P) and 17, 16 (M)
+};
+
+// Pair values of 19 populations in the paper's order (Eq. velocityd3qq19).
+template <typename R>
+__host__ __device__ constexpr Pairs<R> to_pairs(const R (&d)[Q]) {
+  Pairs<R> p{};
+  p.d0 = d[0];
+  p.sAx = d[1] + d[2];
+  p.tAx = d[1] - d[2];
+  p.sAy = d[3] + d[4];
+  p.tAy = d[3] - d[4];
+  p.sAz = d[5] + d[6];
+  p.tAz = d[5] - d[6];
+  {
+    const R sP = d[7] + d[10], tP = d[7] - d[10], sM = d[9] + d[8], tM = d[9] - d[8];
+    p.Dxxyy = sP + sM;
+    p.Dxy = sP - sM;
+    p.Dxyy = tP + tM;
+    p.Dxxy = tP - tM;
   }
-  int c = j == 9 ? 8 : j == 16 ? 1 : 0;  // C9 = 8 g9 + g16
-  if (z == 0)  // xy: 2 g8 + g17 + g18 + xy g4; odd x (g10 + g13) + y (g11 - g14)
-    c += j == 8 ? 2 : (j == 17 || j == 18) ? 1 : j == 4 ? x * y : (j == 10 || j == 13) ? x
-         : j == 11 ? y : j == 14 ? -y : 0;
-  else if (y == 0)  // xz: g7 - g8 + g17 - g18 + xz g5; odd x (g10 - g13) + z (g12 + g15)
-    c += j == 7 ? 1 : j == 8 ? -1 : j == 17 ? 1 : j == 18 ? -1 : j == 5 ? x * z : j == 10 ? x
-         : j == 13 ? -x : (j == 12 || j == 15) ? z : 0;
-  else  // yz: -g7 - g8 - 2 g17 + yz g6; odd y (g11 + g14) + z (g12 - g15)
-    c += (j == 7 || j == 8) ? -1 : j == 17 ? -2 : j == 6 ? y * z : (j == 11 || j == 14) ? y
-         : j == 12 ? z : j == 15 ? -z : 0;
-  return c;
+  {
+    const R sP = d[11] + d[14], tP = d[11] - d[14], sM = d[13] + d[12], tM = d[13] - d[12];
+    p.Dxxzz = sP + sM;
+    p.Dxz = sP - sM;
+    p.Dxzz = tP + tM;
+    p.Dxxz = tP - tM;
+  }
+  {
+    const R sP = d[15] + d[18], tP = d[15] - d[18], sM = d[17] + d[16], tM = d[17] - d[16];
+    p.Dyyzz = sP + sM;
+    p.Dyz = sP - sM;
+    p.Dyzz = tP + tM;
+    p.Dyyz = tP - tM;
+  }
+  return p;
 }
-constexpr bool grouping_is_K() {
-  for (int q = 0; q < Q; ++q)
-    for (int j = 4; j < Q; ++j)
-      if (grouped_coef(q, j) != kb(j, cx(q), cy(q), cz(q))) return false;
+
+// Four populations of a coordinate plane from its four moments plus the
+// plane's part of K g^ (Eq. cascadedcollision1): E (shared by the plane),
+// Ex (the product moment g4/g5/g6) and the two odd sums Oa, Ob.  With
+// q1 = Dii jj/4 + E, q2 = Dij/4 + Ex, q3 = Dijj/4 + Oa, q4 = Diij/4 + Ob the
+// populations are P+ = q1+q2+q3+q4, P- = q1+q2-q3-q4, M+ = q1-q2+q3-q4,
+// M- = q1-q2-q3+q4 (P+, P-: the pair with e_i e_j = +1, positive and
+// negative e_i; M+, M-: the other pair, positive and negative e_i).
+template <typename R>
+__host__ __device__ constexpr void plane_out(R Diijj, R Dij, R Dijj, R Diij, R E, R Ex, R Oa,
+                                             R Ob, R& Pp, R& Pm, R& Mp, R& Mm) {
+  const R q1 = R(0.25) * Diijj + E, q2 = R(0.25) * Dij + Ex;
+  const R q3 = R(0.25) * Dijj + Oa, q4 = R(0.25) * Diij + Ob;
+  const R a = q1 + q2, b = q1 - q2, c = q3 + q4, e = q3 - q4;
+  Pp = a + c;
+  Pm = a - c;
+  Mp = b + e;
+  Mm = b - e;
+}
+
+// Populations f~ = f + K g^ from the pair values of f and g^_4..g^_18
+// (entries 0..3 of g unused): the columns of K grouped by velocity class
+// (Sec. 2, the basis vectors).  The rest node; the three axis pairs, which
+// share -11 g9 - 4 g16; and the three coordinate planes of diagonal
+// velocities, which share 8 g9 + g16.  In a plane the four velocities differ
+// only in the sign of the plane's product moment g4/g5/g6 and of two odd
+// sums, e.g. in the xy plane g10 + g13 (odd in x) and g11 - g14 (odd in y).
+template <typename R>
+__host__ __device__ constexpr void from_pairs(const Pairs<R>& p, const R (&g)[Q], R (&d)[Q]) {
+  d[0] = p.d0 + (R(-30) * g[9] + R(12) * g[16]);
+  const R Ca = R(-11) * g[9] - R(4) * g[16];
+  {
+    const R hs = R(0.5) * p.sAx + (Ca + (g[7] + g[8]) - R(4) * g[17]);
+    const R ht = R(0.5) * p.tAx - R(4) * g[10];
+    d[1] = hs + ht;
+    d[2] = hs - ht;
+  }
+  {
+    const R hs = R(0.5) * p.sAy + (Ca + (g[8] - g[7]) + R(2) * (g[17] - g[18]));
+    const R ht = R(0.5) * p.tAy - R(4) * g[11];
+    d[3] = hs + ht;
+    d[4] = hs - ht;
+  }
+  {
+    const R hs = R(0.5) * p.sAz + (Ca - R(2) * g[8] + R(2) * (g[17] + g[18]));
+    const R ht = R(0.5) * p.tAz - R(4) * g[12];
+    d[5] = hs + ht;
+    d[6] = hs - ht;
+  }
+  const R C9 = R(8) * g[9] + g[16];
+  plane_out(p.Dxxyy, p.Dxy, p.Dxyy, p.Dxxy, C9 + R(2) * g[8] + (g[17] + g[18]), g[4],
+            g[10] + g[13], g[11] - g[14], d[7], d[10], d[9], d[8]);
+  plane_out(p.Dxxzz, p.Dxz, p.Dxzz, p.Dxxz, C9 + (g[7] - g[8]) + (g[17] - g[18]), g[5],
+            g[10] - g[13], g[12] + g[15], d[11], d[14], d[13], d[12]);
+  plane_out(p.Dyyzz, p.Dyz, p.Dyzz, p.Dyyz, C9 - (g[7] + g[8]) - R(2) * g[17], g[6],
+            g[11] + g[14], g[12] - g[15], d[15], d[18], d[17], d[16]);
+}
+
+// Compile-time checks of the pair space against the basis definitions:
+// the populations come back unchanged from their pair values, and a unit
+// g^_j adds column j of K to them.
+constexpr bool pairs_roundtrip() {
+  for (int q = 0; q < Q; ++q) {
+    double d[Q] = {}, out[Q] = {}, g[Q] = {};
+    d[q] = 1.0;
+    from_pairs(to_pairs(d), g, out);
+    for (int k = 0; k < Q; ++k)
+      if (out[k] != (k == q ? 1.0 : 0.0)) return false;
+  }
   return true;
 }
-static_assert(grouping_is_K(), "the grouped back-transform must reproduce K");
+constexpr bool pairs_add_K() {
+  for (int j = 4; j < Q; ++j) {
+    double d[Q] = {}, out[Q] = {}, g[Q] = {};
+    g[j] = 1.0;
+    from_pairs(to_pairs(d), g, out);
+    for (int q = 0; q < Q; ++q)
+      if (out[q] != double(kb(j, cx(q), cy(q), cz(q)))) return false;
+  }
+  return true;
+}
+static_assert(pairs_roundtrip(), "pair values must give back the populations");
+static_assert(pairs_add_K(), "the pair-space back-transform must add the columns of K");
+
+// Half the pair values of the source S_a = w_a [3 e.F + 9 (e.u)(e.F) - 3 u.F]
+// of the symmetric force split (reading of the deferred forcing: its moments
+// are 0, F and uF + Fu).  Summed over each pair and plane with the D3Q19
+// weights (1/3, 1/18, 1/36) they are, with a_i = u_i F_i and t = u.F / 3:
+//   rest -u.F; axis i: s = a_i - t, d = F_i / 3;
+//   plane ij: Diijj = a_i + a_j - t, Dij = u_i F_j + u_j F_i,
+//             Dijj = F_i / 3, Diij = F_j / 3.
+template <typename R, typename T>
+__device__ __forceinline__ void add_half_source(Pairs<R>& p, R ux, R uy, R uz,
+                                                const T (&F)[3]) {
+  const R ax = ux * R(F[0]), ay = uy * R(F[1]), az = uz * R(F[2]);
+  const R uF = ax + ay + az;
+  const R ht = R(1.0 / 6.0) * uF;  // t / 2
+  const R f6x = R(T(F[0]) * T(1.0 / 6.0)), f6y = R(T(F[1]) * T(1.0 / 6.0)),
+          f6z = R(T(F[2]) * T(1.0 / 6.0));
+  p.d0 -= R(0.5) * uF;
+  p.sAx += R(0.5) * ax - ht;
+  p.sAy += R(0.5) * ay - ht;
+  p.sAz += R(0.5) * az - ht;
+  p.tAx += f6x;
+  p.tAy += f6y;
+  p.tAz += f6z;
+  p.Dxxyy += R(0.5) * (ax + ay) - ht;
+  p.Dxxzz += R(0.5) * (ax + az) - ht;
+  p.Dyyzz += R(0.5) * (ay + az) - ht;
+  p.Dxy += R(0.5) * (ux * R(F[1]) + uy * R(F[0]));
+  p.Dxz += R(0.5) * (ux * R(F[2]) + uz * R(F[0]));
+  p.Dyz += R(0.5) * (uy * R(F[2]) + uz * R(F[1]));
+  p.Dxyy += f6x;
+  p.Dxzz += f6x;
+  p.Dxxy += f6y;
+  p.Dyzz += f6y;
+  p.Dxxz += f6z;
+  p.Dyyz += f6z;
+}
 
 // Collide one node.  d[19] holds the pre-collision deviations on entry and
 // the post-collision deviations f~ - w rho0 on return.
@@ -188,83 +385,38 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
                                         R (&d)[Q], NodeOut<R>& out) {
   using T = typename ScalarOf<R>::type;
   // ---- mass and momentum (Eqs. hydrodynamicfields1/2) -------------------
-  // Everything below the populations is formed from the nine +/- pairs: the
-  // axis pairs (sum sA, difference tA) and, in each coordinate plane, the
-  // two diagonal pairs P (e_i e_j = +1) and M (e_i e_j = -1), whose sums and
-  // differences give that plane's moments directly, e.g. in the xy plane
-  //   D_xxyy = sP + sM, D_xy = sP - sM, D_xyy = tP + tM, D_xxy = tP - tM.
-  static_assert(opp(1) == 2 && opp(3) == 4 && opp(5) == 6 && opp(7) == 10 && opp(9) == 8 &&
-                    opp(11) == 14 && opp(13) == 12 && opp(15) == 18 && opp(17) == 16,
-                "pair layout");
   static_assert(cx(1) == 1 && cy(3) == 1 && cz(5) == 1 && cx(7) == 1 && cy(7) == 1 &&
                     cx(9) == 1 && cy(9) == -1 && cx(11) == 1 && cz(11) == 1 && cx(13) == 1 &&
                     cz(13) == -1 && cy(15) == 1 && cz(15) == 1 && cy(17) == 1 && cz(17) == -1,
                 "pair members");
-  R sAx, sAy, sAz, tAx, tAy, tAz;
-  R Dxy, Dxz, Dyz, Dxyy, Dxzz, Dxxy, Dyzz, Dxxz, Dyyz, Dxxyy, Dxxzz, Dyyzz;
-  auto pair_moments = [&]() {
-    sAx = d[1] + d[2];
-    tAx = d[1] - d[2];
-    sAy = d[3] + d[4];
-    tAy = d[3] - d[4];
-    sAz = d[5] + d[6];
-    tAz = d[5] - d[6];
-    {
-      const R sP = d[7] + d[10], tP = d[7] - d[10], sM = d[9] + d[8], tM = d[9] - d[8];
-      Dxxyy = sP + sM;
-      Dxy = sP - sM;
-      Dxyy = tP + tM;
-      Dxxy = tP - tM;
-    }
-    {
-      const R sP = d[11] + d[14], tP = d[11] - d[14], sM = d[13] + d[12], tM = d[13] - d[12];
-      Dxxzz = sP + sM;
-      Dxz = sP - sM;
-      Dxzz = tP + tM;
-      Dxxz = tP - tM;
-    }
-    {
-      const R sP = d[15] + d[18], tP = d[15] - d[18], sM = d[17] + d[16], tM = d[17] - d[16];
-      Dyyzz = sP + sM;
-      Dyz = sP - sM;
-      Dyzz = tP + tM;
-      Dyyz = tP - tM;
-    }
-  };
-  pair_moments();
-  const R drho = d[0] + (sAx + sAy + sAz) + (Dxxyy + Dxxzz + Dyyzz);
-  const R jx = tAx + (Dxyy + Dxzz), jy = tAy + (Dxxy + Dyzz), jz = tAz + (Dxxz + Dyyz);
+  Pairs<R> p = to_pairs(d);
+  const R drho = p.d0 + (p.sAx + p.sAy + p.sAz) + (p.Dxxyy + p.Dxxzz + p.Dyyzz);
+  const R jx = p.tAx + (p.Dxyy + p.Dxzz), jy = p.tAy + (p.Dxxy + p.Dyzz),
+          jz = p.tAz + (p.Dxxz + p.Dyyz);
   const R rho = R(C.rho0) + drho;
   const R rinv = rrcp<R>(rho);
   R ux, uy, uz;
   if (FORCE) {
     // Symmetric split of the body force: the velocity is (j + F/2)/rho and
-    // half of the source S_a = w_a [3 e.F + 9 (e.u)(e.F) - 3 u.F] is added
-    // before the collision (its moments are 0, F and uF + Fu).
+    // half of the source is added before the collision, half after.
     ux = (jx + R(T(0.5) * C.F[0])) * rinv;
     uy = (jy + R(T(0.5) * C.F[1])) * rinv;
     uz = (jz + R(T(0.5) * C.F[2])) * rinv;
+    add_half_source(p, ux, uy, uz, C.F);
   } else {
     ux = jx * rinv;
     uy = jy * rinv;
     uz = jz * rinv;
   }
-  R Sa[FORCE ? Q : 1];
-  if (FORCE) {
-    const R uF = ux * R(C.F[0]) + uy * R(C.F[1]) + uz * R(C.F[2]);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-      const T eF = T(cx(q)) * C.F[0] + T(cy(q)) * C.F[1] + T(cz(q)) * C.F[2];
-      R eu = R(cx(q)) * ux + R(cy(q)) * uy + R(cz(q)) * uz;
-      Sa[q] = R(wt<T>(q)) * (R(T(3) * eF) + R(T(9) * eF) * eu - R(3) * uF);
-      d[q] += R(0.5) * Sa[q];
-    }
-    pair_moments();
-  }
 
   // ---- raw moments of the deviations (Eq. rawmomentdistributionfunction1)
   // k'_ii = rho0/3 + Dii, k'_ij = Dij, third order k' = D, k'_iijj = rho0/9 + D.
-  const R Dxx = sAx + (Dxxyy + Dxxzz), Dyy = sAy + (Dxxyy + Dyyzz), Dzz = sAz + (Dxxzz + Dyyzz);
+  const R Dxy = p.Dxy, Dxz = p.Dxz, Dyz = p.Dyz;
+  const R Dxyy = p.Dxyy, Dxzz = p.Dxzz, Dxxy = p.Dxxy, Dyzz = p.Dyzz, Dxxz = p.Dxxz,
+          Dyyz = p.Dyyz;
+  const R Dxxyy = p.Dxxyy, Dxxzz = p.Dxxzz, Dyyzz = p.Dyyzz;
+  const R Dxx = p.sAx + (Dxxyy + Dxxzz), Dyy = p.sAy + (Dxxyy + Dyyzz),
+          Dzz = p.sAz + (Dxxzz + Dyyzz);
 
   const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
   const R r3 = R(C.rho0 * T(1.0 / 3.0));
@@ -290,12 +442,14 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
 
   // ---- change of moments, Eqs. collisionkernelg4..g18 --------------------
   // omega_4..8 = w (Sec. 3.1); omega_9..18 from the constants above (1 in Sec. 3.1).
-  const R g4 = R(-0.25) * w * m4;
-  const R g5 = R(-0.25) * w * m5;
-  const R g6 = R(-0.25) * w * m6;
-  const R g7 = R(-1.0 / 12.0) * w * m7;
-  const R g8 = R(-1.0 / 36.0) * w * (R(2) * m8 - m7);
-  const R g9 = R(C.c9) * m9;
+  R g[Q];
+  g[4] = R(-0.25) * w * m4;
+  g[5] = R(-0.25) * w * m5;
+  g[6] = R(-0.25) * w * m6;
+  g[7] = R(-1.0 / 12.0) * w * m7;
+  g[8] = R(-1.0 / 36.0) * w * (R(2) * m8 - m7);
+  g[9] = R(C.c9) * m9;
+  const R g4 = g[4], g5 = g[5], g6 = g[6], g7 = g[7], g8 = g[8], g9 = g[9];
 
   // g^_10..15 in +/- pairs: with the row sums
   //   Xy = ux k'yy - k'xyy + 2 uy k'xy - 2 rho ux uy^2 (and Xz, Yx, Yz, Zx, Zy
@@ -313,12 +467,13 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
   const R a4y = uy * g4, a5z = uz * g5, a4x = ux * g4, a6z = uz * g6, a5x = ux * g5, a6y = uy * g6;
   const R hx = R(0.75) * ux, hy = R(0.75) * uy, hz = R(1.5) * uz;
   const R w9 = R(14) * g9;
-  const R g10 = R(C.c10) * (Xy + Xz) + (a4y + a5z) + hx * (w9 - (g7 + g8));
-  const R g13 = R(C.c13) * (Xy - Xz) + (a4y - a5z) + hx * (R(3) * g8 - g7);
-  const R g11 = R(C.c11) * (Yx + Yz) + (a4x + a6z) + hy * (w9 + (g7 - g8));
-  const R g14 = R(C.c14) * (Yz - Yx) + (a6z - a4x) - hy * (g7 + R(3) * g8);
-  const R g12 = R(C.c12) * (Zx + Zy) + (a5x + a6y) + hz * (g8 + R(7) * g9);
-  const R g15 = R(C.c15) * (Zx - Zy) + (a5x - a6y) + hz * g7;
+  g[10] = R(C.c10) * (Xy + Xz) + (a4y + a5z) + hx * (w9 - (g7 + g8));
+  g[13] = R(C.c13) * (Xy - Xz) + (a4y - a5z) + hx * (R(3) * g8 - g7);
+  g[11] = R(C.c11) * (Yx + Yz) + (a4x + a6z) + hy * (w9 + (g7 - g8));
+  g[14] = R(C.c14) * (Yz - Yx) + (a6z - a4x) - hy * (g7 + R(3) * g8);
+  g[12] = R(C.c12) * (Zx + Zy) + (a5x + a6y) + hz * (g8 + R(7) * g9);
+  g[15] = R(C.c15) * (Zx - Zy) + (a5x - a6y) + hz * g7;
+  const R g10 = g[10], g11 = g[11], g12 = g[12], g13 = g[13], g14 = g[14], g15 = g[15];
 
   // Post-collision diagonal central moments k~ii = rho/3 + a_i (the <K g^|e_i^2>
   // rows of Eq. momentscascadedcollisionterm added to k'_ii - rho u_i^2), and
@@ -350,89 +505,22 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
   // shared products: ux uy g4, ux uz g5, uy uz g6 and ux g10, uy g11, uz g12
   const R p4 = ux * a4y, p5 = ux * a5z, p6 = uy * a6z;
   const R v10 = ux * g10, v11 = uy * g11, v12 = uz * g12;
-  const R g16 = R(C.c16) * b16 - R(4.0 / 3.0) * (p4 + p5 + p6) +
-                R(0.5) * (ux2 - uy2) * g7 + R(0.5) * (ux2 + uy2 - R(2) * uz2) * g8 +
-                (R(-7) * (ux2 + uy2 + uz2) - R(8)) * g9 + R(4.0 / 3.0) * (v10 + v11 + v12);
-  const R g17 = R(C.c17) * b17 - R(2.0 / 3.0) * (p4 + p5) + R(4.0 / 3.0) * p6 +
-                R(0.25) * (ux2 - uy2 - R(3) * uz2 - R(2)) * g7 +
-                R(0.25) * (ux2 - R(5) * uy2 + uz2 - R(2)) * g8 +
-                R(1.75) * (R(-2) * ux2 + uy2 + uz2) * g9 + R(2.0 / 3.0) * v10 -
-                third * (v11 + v12) - uy * g14 + uz * g15;
-  const R g18 = R(C.c18) * b18 - R(2) * (p4 - p5) +
-                R(0.75) * (ux2 - uy2 + uz2 + R(2.0 / 3.0)) * g7 +
-                R(0.75) * (R(-3) * ux2 - uy2 + uz2 - R(2)) * g8 + R(5.25) * (uz2 - uy2) * g9 +
-                (v11 - v12) + R(2) * ux * g13 - uy * g14 - uz * g15;
+  g[16] = R(C.c16) * b16 - R(4.0 / 3.0) * (p4 + p5 + p6) +
+          R(0.5) * (ux2 - uy2) * g7 + R(0.5) * (ux2 + uy2 - R(2) * uz2) * g8 +
+          (R(-7) * (ux2 + uy2 + uz2) - R(8)) * g9 + R(4.0 / 3.0) * (v10 + v11 + v12);
+  g[17] = R(C.c17) * b17 - R(2.0 / 3.0) * (p4 + p5) + R(4.0 / 3.0) * p6 +
+          R(0.25) * (ux2 - uy2 - R(3) * uz2 - R(2)) * g7 +
+          R(0.25) * (ux2 - R(5) * uy2 + uz2 - R(2)) * g8 +
+          R(1.75) * (R(-2) * ux2 + uy2 + uz2) * g9 + R(2.0 / 3.0) * v10 -
+          third * (v11 + v12) - uy * g14 + uz * g15;
+  g[18] = R(C.c18) * b18 - R(2) * (p4 - p5) +
+          R(0.75) * (ux2 - uy2 + uz2 + R(2.0 / 3.0)) * g7 +
+          R(0.75) * (R(-3) * ux2 - uy2 + uz2 - R(2)) * g8 + R(5.25) * (uz2 - uy2) * g9 +
+          (v11 - v12) + R(2) * ux * g13 - uy * g14 - uz * g15;
 
   // ---- back-transform f~ = f + K g^ (+ second half of the source) --------
-  // Columns of K grouped by velocity class (Sec. 2, the basis vectors): the
-  // rest node; the three axis pairs, which share -11 g9 - 4 g16; and the
-  // three coordinate planes of diagonal velocities, which share 8 g9 + g16.
-  // In a plane the four velocities differ only in the sign of the plane's
-  // product moment g4/g5/g6 (even part) and of two odd sums, e.g. in the xy
-  // plane Px = g10 + g13 (odd in x) and Py = g11 - g14 (odd in y).
-  static_assert(cx(7) == 1 && cy(7) == 1 && cx(8) == -1 && cy(8) == 1 && cx(9) == 1 &&
-                    cy(9) == -1 && cx(10) == -1 && cy(10) == -1,
-                "xy-plane velocity order");
-  static_assert(cx(11) == 1 && cz(11) == 1 && cx(12) == -1 && cz(12) == 1 && cx(13) == 1 &&
-                    cz(13) == -1 && cx(14) == -1 && cz(14) == -1,
-                "xz-plane velocity order");
-  static_assert(cy(15) == 1 && cz(15) == 1 && cy(16) == -1 && cz(16) == 1 && cy(17) == 1 &&
-                    cz(17) == -1 && cy(18) == -1 && cz(18) == -1,
-                "yz-plane velocity order");
-  static_assert(cx(1) == 1 && cx(2) == -1 && cy(3) == 1 && cy(4) == -1 && cz(5) == 1 &&
-                    cz(6) == -1,
-                "axis velocity order");
-  static_assert(kb(9, 0, 0, 0) == -30 && kb(16, 0, 0, 0) == 12 && kb(9, 1, 0, 0) == -11 &&
-                    kb(16, 1, 0, 0) == -4 && kb(9, 1, 1, 0) == 8 && kb(16, 1, 1, 0) == 1,
-                "K entries of the grouping");
-  d[0] += R(-30) * g9 + R(12) * g16;
-  const R Ca = R(-11) * g9 - R(4) * g16;
-  {
-    const R Ex = Ca + (g7 + g8) - R(4) * g17;
-    d[1] = (d[1] + Ex) - R(4) * g10;
-    d[2] = (d[2] + Ex) + R(4) * g10;
-    const R Ey = Ca + (g8 - g7) + R(2) * (g17 - g18);
-    d[3] = (d[3] + Ey) - R(4) * g11;
-    d[4] = (d[4] + Ey) + R(4) * g11;
-    const R Ez = Ca - R(2) * g8 + R(2) * (g17 + g18);
-    d[5] = (d[5] + Ez) - R(4) * g12;
-    d[6] = (d[6] + Ez) + R(4) * g12;
-  }
-  const R C9 = R(8) * g9 + g16;
-  {
-    const R E = C9 + R(2) * g8 + (g17 + g18);
-    const R Ep = E + g4, Em = E - g4;
-    const R Px = g10 + g13, Py = g11 - g14;
-    const R S = Px + Py, D = Py - Px;
-    d[7] += Ep + S;
-    d[10] += Ep - S;
-    d[8] += Em + D;
-    d[9] += Em - D;
-  }
-  {
-    const R E = C9 + (g7 - g8) + (g17 - g18);
-    const R Ep = E + g5, Em = E - g5;
-    const R Qx = g10 - g13, Qz = g12 + g15;
-    const R S = Qx + Qz, D = Qz - Qx;
-    d[11] += Ep + S;
-    d[14] += Ep - S;
-    d[12] += Em + D;
-    d[13] += Em - D;
-  }
-  {
-    const R E = C9 - (g7 + g8) - R(2) * g17;
-    const R Ep = E + g6, Em = E - g6;
-    const R Ry = g11 + g14, Rz = g12 - g15;
-    const R S = Ry + Rz, D = Rz - Ry;
-    d[15] += Ep + S;
-    d[18] += Ep - S;
-    d[16] += Em + D;
-    d[17] += Em - D;
-  }
-  if (FORCE) {
-#pragma unroll
-    for (int q = 0; q < Q; ++q) d[q] += R(0.5) * Sa[q];
-  }
+  if (FORCE) add_half_source(p, ux, uy, uz, C.F);
+  from_pairs(p, g, d);
   out.rho = rho;
   out.ux = ux;
   out.uy = uy;

@@ -51,10 +51,14 @@ __host__ __device__ __forceinline__ CollideConst<R> make_const(const PhysParams&
   C.F[2] = R(P.F[2]);
   C.K3 = R(3.0 * P.K);
   C.logK3 = R(P.logK3);
+  C.log2K3 = R(P.logK3 * 1.4426950408889634074);
   C.n = R(P.n);
+  C.rn = R(1.0 / P.n);
   C.ehalf = R(0.5 * (P.n - 1.0));
   C.ylo = R(P.ylo);
   C.yhi = R(P.yhi);
+  C.ylo2 = R(P.ylo * 1.4426950408889634074);
+  C.yhi2 = R(P.yhi * 1.4426950408889634074);
   C.nu_min = R(P.nu_min);
   C.nu_max = R(P.nu_max);
   C.newtonian = P.newtonian;
