@@ -69,7 +69,7 @@ __device__ __forceinline__ void batch_node(const LatDesc<R>& L, const S* __restr
     pull_face<S, R>(src, L.qstride, L.nx, L.ny, L.nz, pitch, plane, L.facebits, x, y, z, i,
                     L.lidc, d);
   }
-  collide<R, FORCE>(L.C, d, o);
+  collide<R, FORCE, pair_out<S>()>(L.C, d, o);
 #pragma unroll
   for (int q = 0; q < Q; ++q) dst[q * qs + i] = Codec<S, R>::enc(d[q], R(1));
 }

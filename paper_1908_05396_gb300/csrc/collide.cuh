@@ -378,9 +378,115 @@ __device__ __forceinline__ void add_half_source(Pairs<R>& p, R ux, R uy, R uz,
   p.Dyyz += f6z;
 }
 
+// Post-collision populations f~ = f + K g^ (+ S, the whole body-force source
+// of the symmetric split: half before and half after the collision), added
+// to the pre-collision deviations as one correction per population, so that
+// each population is rounded once at its own scale.  The correction is
+// grouped by velocity class as in from_pairs.  With FP32 populations this
+// matters: rebuilding them from pair values rounds sums of populations each
+// step, and near a steady state those roundings repeat and accumulate.
+// For a +/- pair (e, -e) the source is S_+- = w [9 (e.u)(e.F) - 3 u.F] +- 3 w e.F.
+template <typename R, bool FORCE, typename T>
+__host__ __device__ constexpr void add_K_g(R (&d)[Q], const R (&g)[Q], R ux, R uy, R uz,
+                                           const T (&F)[3]) {
+  R se = R(0), so = R(0), uF = R(0);
+  if (FORCE) uF = ux * R(F[0]) + uy * R(F[1]) + uz * R(F[2]);
+  d[0] += (R(-30) * g[9] + R(12) * g[16]) - (FORCE ? uF : R(0));
+  const R Ca = R(-11) * g[9] - R(4) * g[16];
+  const R u6 = R(1.0 / 6.0) * uF;  // 3 w u.F for the axis weight 1/18
+  {
+    const R E = Ca + (g[7] + g[8]) - R(4) * g[17];
+    const R O = R(4) * g[10];
+    if (FORCE) { se = R(0.5) * ux * R(F[0]) - u6; so = R(T(F[0]) * T(1.0 / 6.0)); }
+    d[1] += (E - O) + (se + so);
+    d[2] += (E + O) + (se - so);
+  }
+  {
+    const R E = Ca + (g[8] - g[7]) + R(2) * (g[17] - g[18]);
+    const R O = R(4) * g[11];
+    if (FORCE) { se = R(0.5) * uy * R(F[1]) - u6; so = R(T(F[1]) * T(1.0 / 6.0)); }
+    d[3] += (E - O) + (se + so);
+    d[4] += (E + O) + (se - so);
+  }
+  {
+    const R E = Ca - R(2) * g[8] + R(2) * (g[17] + g[18]);
+    const R O = R(4) * g[12];
+    if (FORCE) { se = R(0.5) * uz * R(F[2]) - u6; so = R(T(F[2]) * T(1.0 / 6.0)); }
+    d[5] += (E - O) + (se + so);
+    d[6] += (E + O) + (se - so);
+  }
+  const R C9 = R(8) * g[9] + g[16];
+  const R u12 = R(1.0 / 12.0) * uF;  // 3 w u.F for the diagonal weight 1/36
+  // One plane: pair P = (Pp, Pm) with e_i e_j = +1 and M = (Mp, Mm) with
+  // e_i e_j = -1 (first member positive along the plane's first axis); its
+  // part of K g^ is E +- Ex (product moment) plus the odd sums (Oa, Ob), and
+  // ea/eb, ua/ub are e.F and e.u of the P and M pairs' positive members.
+  auto plane = [&](R& Pp, R& Pm, R& Mp, R& Mm, R E, R Ex, R Oa, R Ob, R fP, R fM, R vP,
+                   R vM) {
+    const R Ep = E + Ex, Em = E - Ex;
+    const R Sg = Oa + Ob, Dg = Ob - Oa;
+    R sP = R(0), oP = R(0), sM = R(0), oM = R(0);
+    if (FORCE) {
+      sP = R(0.25) * vP * fP - u12;
+      oP = R(1.0 / 12.0) * fP;
+      sM = R(0.25) * vM * fM - u12;
+      oM = R(1.0 / 12.0) * fM;
+    }
+    Pp += (Ep + Sg) + (sP + oP);
+    Pm += (Ep - Sg) + (sP - oP);
+    Mp += (Em - Dg) + (sM + oM);
+    Mm += (Em + Dg) + (sM - oM);
+  };
+  const R Fx = FORCE ? R(F[0]) : R(0), Fy = FORCE ? R(F[1]) : R(0), Fz = FORCE ? R(F[2]) : R(0);
+  plane(d[7], d[10], d[9], d[8], C9 + R(2) * g[8] + (g[17] + g[18]), g[4], g[10] + g[13],
+        g[11] - g[14], Fx + Fy, Fx - Fy, ux + uy, ux - uy);
+  plane(d[11], d[14], d[13], d[12], C9 + (g[7] - g[8]) + (g[17] - g[18]), g[5], g[10] - g[13],
+        g[12] + g[15], Fx + Fz, Fx - Fz, ux + uz, ux - uz);
+  plane(d[15], d[18], d[17], d[16], C9 - (g[7] + g[8]) - R(2) * g[17], g[6], g[11] + g[14],
+        g[12] - g[15], Fy + Fz, Fy - Fz, uy + uz, uy - uz);
+}
+
+// Compile-time checks of the additive back-transform: a unit g^_j adds
+// column j of K, and the body-force correction equals the source
+// w_a [3 e.F + 9 (e.u)(e.F) - 3 u.F] of every direction.
+constexpr bool add_K_g_is_K() {
+  for (int j = 4; j < Q; ++j) {
+    double d[Q] = {}, g[Q] = {};
+    const double F[3] = {0.0, 0.0, 0.0};
+    g[j] = 1.0;
+    add_K_g<double, false>(d, g, 0.0, 0.0, 0.0, F);
+    for (int q = 0; q < Q; ++q)
+      if (d[q] != double(kb(j, cx(q), cy(q), cz(q)))) return false;
+  }
+  return true;
+}
+constexpr bool add_K_g_source() {
+  const double F[3] = {0.375, -0.625, 0.8125};
+  const double u[3] = {0.25, 0.5, -0.125};
+  double d[Q] = {}, g[Q] = {};
+  add_K_g<double, true>(d, g, u[0], u[1], u[2], F);
+  for (int q = 0; q < Q; ++q) {
+    const double eF = cx(q) * F[0] + cy(q) * F[1] + cz(q) * F[2];
+    const double eu = cx(q) * u[0] + cy(q) * u[1] + cz(q) * u[2];
+    const double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+    const double S = wt<double>(q) * (3.0 * eF + 9.0 * eu * eF - 3.0 * uF);
+    const double diff = d[q] - S;
+    if (diff > 1e-15 || diff < -1e-15) return false;
+  }
+  return true;
+}
+static_assert(add_K_g_is_K(), "the additive back-transform must add the columns of K");
+static_assert(add_K_g_source(), "the additive back-transform must add the body-force source");
+
 // Collide one node.  d[19] holds the pre-collision deviations on entry and
 // the post-collision deviations f~ - w rho0 on return.
-template <typename R, bool FORCE>
+// PAIR_OUT selects how the populations are written back: rebuilt from the
+// pair values (fewer registers: the 19 inputs are dead after the pair values
+// are formed), which is exact when the inputs are FP16 values decoded to FP32
+// (sums of a few of them need no rounding), or as one correction added to
+// each input population (add_K_g), which keeps FP32 populations to a single
+// rounding per step.
+template <typename R, bool FORCE, bool PAIR_OUT = false>
 __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>::type>& C,
                                         R (&d)[Q], NodeOut<R>& out) {
   using T = typename ScalarOf<R>::type;
@@ -519,8 +625,12 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
           (v11 - v12) + R(2) * ux * g13 - uy * g14 - uz * g15;
 
   // ---- back-transform f~ = f + K g^ (+ second half of the source) --------
-  if (FORCE) add_half_source(p, ux, uy, uz, C.F);
-  from_pairs(p, g, d);
+  if constexpr (PAIR_OUT) {
+    if (FORCE) add_half_source(p, ux, uy, uz, C.F);
+    from_pairs(p, g, d);
+  } else {
+    add_K_g<R, FORCE>(d, g, ux, uy, uz, C.F);
+  }
   out.rho = rho;
   out.ux = ux;
   out.uy = uy;

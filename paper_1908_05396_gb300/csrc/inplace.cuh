@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_aa_kernel(const StepArg
                        a.lidc, d);
     }
     NodeOut<R> o;
-    collide<R, FORCE>(a.C, d, o);
+    collide<R, FORCE, pair_out<S>()>(a.C, d, o);
     if (LIN == 1) {
 #pragma unroll
       for (int q = 0; q < Q; ++q) a.dstq[q][i] = Codec<S, R>::enc(d[q], R(1));
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(256) fields_aa_kernel(const S* __restrict__ A,
   aa_read<S, R, L>(A, g.qstride, x, y, z, i, g.nx, g.ny, g.nz, g.pitch, int(g.plane), g.facebits,
                    lidc, d);
   NodeOut<R> o;
-  collide<R, FORCE>(C, d, o);
+  collide<R, FORCE, pair_out<S>()>(C, d, o);
   const int64_t N = int64_t(g.nx) * g.ny * g.nz;
   const int64_t k = (int64_t(z) * g.ny + y) * g.nx + x;
   if (rho) rho[k] = double(o.rho);

@@ -42,6 +42,15 @@ template <typename R> struct Codec<__half, R> {
   }
 };
 
+// Whether the collision rebuilds the populations of storage type S from its
+// pair values (see collide): for FP16 storage, whose decoded values sum
+// without rounding, and for FP64, whose rounding stays far below every
+// tolerance; FP32 storage takes one added correction per population.
+template <typename S>
+__host__ __device__ constexpr bool pair_out() {
+  return std::is_same<S, __half>::value || std::is_same<S, double>::value;
+}
+
 template <typename R>
 __host__ __device__ __forceinline__ CollideConst<R> make_const(const PhysParams& P) {
   CollideConst<R> C;
@@ -299,7 +308,7 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_kernel(const StepArgs<S
                       i, a.lidc, d);
     }
     NodeOut<R> o;
-    collide<R, FORCE>(a.C, d, o);
+    collide<R, FORCE, pair_out<S>()>(a.C, d, o);
 #pragma unroll
     for (int q = 0; q < Q; ++q) a.dstq[q][i] = Codec<S, R>::enc(d[q], R(1));
     if (CHECK) {
@@ -386,7 +395,7 @@ __global__ void __launch_bounds__(128, CAP ? 4 : 1) step2_kernel(const StepArgs<
       for (int q = 0; q < Q; ++q) d[q] = V2(dA[q], dB[q]);
     }
     NodeOut<V2> o;
-    collide<V2, FORCE>(a.C, d, o);
+    collide<V2, FORCE, pair_out<S>()>(a.C, d, o);
 #pragma unroll
     for (int q = 0; q < Q; ++q) a.dstq[q][iA] = Codec<S, float>::enc(lane0(d[q]), 1.0f);
     if (activeB) {
@@ -442,7 +451,7 @@ __global__ void __launch_bounds__(256) fields_kernel(const S* __restrict__ src, 
   R d[Q];
   pull<S, R>(src, g, x, y, z, i, inv_scale, d);
   NodeOut<R> o;
-  collide<R, FORCE>(C, d, o);
+  collide<R, FORCE, pair_out<S>()>(C, d, o);
   const int64_t N = int64_t(g.nx) * g.ny * g.nz;
   const int64_t k = (int64_t(z) * g.ny + y) * g.nx + x;
   if (rho) rho[k] = double(o.rho);
@@ -470,7 +479,7 @@ __global__ void collide_nodes_kernel(PhysParams P, const double* __restrict__ fi
     d[q] = Codec<S, R>::dec(Codec<S, R>::enc(dev, inv_scale), inv_scale);
   }
   NodeOut<R> o;
-  collide<R, FORCE>(C, d, o);
+  collide<R, FORCE, pair_out<S>()>(C, d, o);
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const R st = Codec<S, R>::dec(Codec<S, R>::enc(d[q], inv_scale), inv_scale);

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256) step_partials_kernel(const S* __restrict_
     R d[Q];
     pull<S, R>(src, g, x, y, z, i, inv_scale, d);
     NodeOut<R> o;
-    collide<R, FORCE>(C, d, o);
+    collide<R, FORCE, pair_out<S>()>(C, d, o);
 #pragma unroll
     for (int q = 0; q < Q; ++q) dst[q * g.qstride + i] = Codec<S, R>::enc(d[q], inv_scale);
     const int64_t nst = g.plane * g.nz;
