@@ -439,7 +439,11 @@ def run_ours(args):
     if not args.no_extra:
         barrier()
         batch = _batch_bench(clbm, torch, wl, args.batch_steps, peak)
-        serving = _serving_bench(clbm, wl, args.serve_requests, args.serve_seq)
+        trace = wl.serving_trace(count=256, seed=0, rate=20.0)[:args.serve_requests]
+        serving = _serving_bench(
+            clbm, trace, 1e-7, args.serve_cap, 20, 100,
+            f"the first {len(trace)} requests of the serving trace: Poisson 20/s (seed 0), half "
+            "cavities L~U{32..192}, half channels 8xU{32..256}x8, Re~U[50,1000], n~U[0.4,1.6]")
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -561,21 +565,25 @@ def _batch_bench(clbm, torch, wl, steps, peak):
             "timing": "host wall clock around graph-captured batch steps, synchronised"}
 
 
-def _serve_trace(clbm, trace, dtype, tol, cap, plateau, keep):
-    """Replay the trace through the continuous-batching server; the first
-    `keep` requests keep their fields."""
-    with clbm.Server(dtype, hbm_budget_bytes=150e9, max_active=64, check_interval=100) as srv:
+def _serve_trace(clbm, trace, dtype, tol, cap, plateau, check):
+    """Replay the trace through the continuous-batching server (requests
+    submitted at their arrival times); every request keeps its fields."""
+    with clbm.Server(dtype, hbm_budget_bytes=150e9, max_active=64, check_interval=check) as srv:
         t0 = time.perf_counter()
         ids = []
-        for k, r in enumerate(trace):
+        for r in trace:
             delay = t0 + r.arrival - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
             ids.append(srv.submit(**r.problem.kwargs(), tol=tol, max_steps=cap,
-                                  plateau_checks=plateau, keep_fields=k < keep))
+                                  plateau_checks=plateau, keep_fields=True))
         res = [srv.wait(i) for i in ids]
-        fields = [srv.fields(i) for i in ids[:keep]]
+        fields = [srv.fields(i)[1] for i in ids]
         info = srv.info()
+    return res, fields, info
+
+
+def _latency_stats(clbm, res) -> dict:
     lat = sorted(r["t_done"] - r["t_submit"] for r in res)
     span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
     status = {}
@@ -583,99 +591,110 @@ def _serve_trace(clbm, trace, dtype, tol, cap, plateau, keep):
         k = clbm.SOLVE_STATUS[r["status"]]
         status[k] = status.get(k, 0) + 1
     q = lambda p: lat[min(len(lat) - 1, int(round(p * (len(lat) - 1))))]
-    out = {"form": dtype, "solves_per_s": len(res) / span, "p50_latency_s": q(0.5),
-           "p99_latency_s": q(0.99), "makespan_s": span, "status": status,
-           "mean_steps": sum(r["steps"] for r in res) / len(res),
-           "server_MLUPS": info["lattice_updates"] / max(info["busy_seconds"], 1e-9) / 1e6}
-    return out, res, fields
+    return {"solves_per_s": len(res) / span, "p50_latency_s": q(0.5), "p99_latency_s": q(0.99),
+            "makespan_s": span, "status": status,
+            "mean_steps": sum(r["steps"] for r in res) / len(res)}
 
 
-def _serving_bench(clbm, wl, n_req, seq_req):
-    """Poisson trace through the continuous-batching server in three storage
-    forms (F16R, F16S, FP32), and the first requests solved one at a time by
-    the plain FP64 solver (the solves/s baseline).  Each served result of
-    those requests is compared with FP64 after the same number of steps."""
+def _solve_alone(clbm, prob, dtype, tol, cap, plateau, check):
+    """One request solved by a plain single-instance handle with the server's
+    stopping rule: R <= tol, divergence, the step cap, or a plateau of the
+    residual (no 10 % drop over `plateau` checks), read at every check."""
+    with clbm.Lattice(**prob.kwargs(), dtype=dtype, check_interval=check) as lt:
+        best, since, steps, status = float("inf"), 0, 0, "max_steps"
+        while steps < cap:
+            lt.step(check)
+            steps += check
+            R, rc = lt.residual()
+            if rc != 0:
+                status = "diverged"
+                break
+            if R <= tol:
+                status = "converged"
+                break
+            if R < 0.9 * best:
+                best, since = R, 0
+            elif R == R and R != float("inf"):
+                since += 1
+            if since >= plateau:
+                status = "plateau"
+                break
+        u = lt.fields()[1] if status != "diverged" else None
+    return status, steps, u
+
+
+def _serving_bench(clbm, trace, tol, cap, plateau, check, workload, bars=None):
+    """The trace through the continuous-batching server in three storage
+    forms (F16R, the headline, F16S and FP32), and the same requests solved
+    one at a time by plain single-instance FP64 handles with the same
+    stopping rule and check interval (the solves/s baseline).  Each served
+    result is compared with the FP64 result of the same request: at the same
+    step count where both stopped on the step cap, else at each one's own end
+    (its steady state when both converged)."""
     import numpy as np
-    trace = wl.serving_trace(count=n_req, seed=0, rate=20.0, cavity_L=(16, 48),
-                             channel_H=(16, 64), Re_range=(50.0, 400.0))
-    tol, cap, plateau = 1e-7, 200_000, 20
-    forms, kept = {}, {}
-    for dt in ("f16r", "f16s", "f32"):
-        forms[dt], res, fields = _serve_trace(clbm, trace, dt, tol, cap, plateau, seq_req)
-        kept[dt] = (res, fields)
-    # sequential FP64 on the first requests: baseline and reference velocities
+    bars = bars or {"f16r": 2e-3, "f16s": 2e-3, "f32": 1e-4}
     t0 = time.perf_counter()
-    ref = []
-    for r in trace[:seq_req]:
-        with clbm.Lattice(**r.problem.kwargs(), dtype="f64", check_interval=100) as lt:
-            best, since, steps, status = float("inf"), 0, 0, "max_steps"
-            while steps < cap:
-                lt.step(100)
-                steps += 100
-                R, rc = lt.residual()
-                if rc != 0:
-                    status = "diverged"
-                    break
-                if R <= tol:
-                    status = "converged"
-                    break
-                if R < 0.9 * best:
-                    best, since = R, 0
-                elif R == R and R != float("inf"):
-                    since += 1
-                if since >= plateau:
-                    status = "plateau"
-                    break
-            ref.append((status, steps))
+    base = [_solve_alone(clbm, r.problem, "f64", tol, cap, plateau, check) for r in trace]
     seq_dt = time.perf_counter() - t0
-    # accuracy: each served result against FP64 after the same number of
-    # steps (one untimed FP64 run per request, sampled at each form's count)
-    bars = {"f16r": 2e-3, "f16s": 2e-3, "f32": 1e-4}
-    l2 = {dt: [] for dt in forms}
-    for k, r in enumerate(trace[:seq_req]):
-        want = sorted({kept[dt][0][k]["steps"] for dt in forms
-                       if clbm.SOLVE_STATUS[kept[dt][0][k]["status"]] != "diverged"})
-        if not want:
-            continue
-        u64 = {}
-        try:
-            with clbm.Lattice(**r.problem.kwargs(), dtype="f64", check_interval=100) as lt:
-                done = 0
-                for n in want:
-                    lt.step(n - done)
-                    done = n
-                    u64[n] = lt.fields()[1]
-        except clbm.CLBMError:
-            pass   # FP64 diverged first: only the counts reached so far are compared
-        for dt in forms:
-            res, fields = kept[dt]
-            if res[k]["steps"] in u64:
-                ref_u = u64[res[k]["steps"]]
-                l2[dt].append(float(np.linalg.norm(fields[k][1] - ref_u) / np.linalg.norm(ref_u)))
-    for dt, out in forms.items():
-        out["velocity_l2_vs_f64"] = l2[dt]
-        out["within_bar"] = f"{sum(x <= bars[dt] for x in l2[dt])}/{len(l2[dt])} at L2 <= {bars[dt]:g}"
-    head = forms["f16r"]
+    base_status = {}
+    for st, _, _ in base:
+        base_status[st] = base_status.get(st, 0) + 1
+    forms = {}
+    for dt in ("f16r", "f16s", "f32"):
+        res, fields, info = _serve_trace(clbm, trace, dt, tol, cap, plateau, check)
+        out = _latency_stats(clbm, res)
+        out["server_MLUPS"] = info["lattice_updates"] / max(info["busy_seconds"], 1e-9) / 1e6
+        l2 = []
+        for r, u, (st, n, u64) in zip(res, fields, base):
+            if u64 is None or clbm.SOLVE_STATUS[r["status"]] == "diverged":
+                continue
+            l2.append(float(np.linalg.norm(u - u64) / max(np.linalg.norm(u64), 1e-300)))
+        out["velocity_l2_vs_f64"] = {"n": len(l2), "median": float(np.median(l2)) if l2 else None,
+                                     "max": max(l2) if l2 else None,
+                                     "within_bar": f"{sum(x <= bars[dt] for x in l2)}/{len(l2)} at "
+                                                   f"L2 <= {bars[dt]:g}"}
+        del fields
+        forms[dt] = out
+    head = dict(forms["f16r"])
     head.update({
-        "workload": f"{n_req} requests, Poisson 20/s (seed 0), half cavities L~U{{16..48}}, "
-                    "half channels 8xU{16..64}x8, Re~U[50,400], n~U[0.4,1.6], FP32 math, "
-                    f"tol {tol}, cap {cap} steps, plateau {plateau} checks",
-        "accuracy_sample": f"velocity L2 of each served result (first {seq_req} requests, not "
-                           "diverged) against the same request stepped in FP64 for the same "
-                           "number of steps",
-        "other_forms": {dt: {k: forms[dt][k] for k in ("solves_per_s", "p50_latency_s",
-                                                       "p99_latency_s", "status",
-                                                       "velocity_l2_vs_f64", "within_bar")}
-                        for dt in ("f16s", "f32")},
-        "sequential_f64_solves_per_s": seq_req / seq_dt,
-        "sequential_f64_sample": f"first {seq_req} requests one at a time, plain FP64 handles, "
-                                 f"statuses {[st for st, _ in ref]}, "
-                                 f"mean {sum(n for _, n in ref) / len(ref):.0f} steps"})
+        "form": "f16r", "workload": workload,
+        "rule": f"tol {tol}, step cap {cap}, plateau {plateau} checks, check interval {check} steps",
+        "other_forms": {dt: forms[dt] for dt in ("f16s", "f32")},
+        "sequential_f64": {"solves_per_s": len(trace) / seq_dt, "seconds": seq_dt,
+                           "status": base_status,
+                           "what": "the same requests one at a time, plain FP64 handles, same rule"},
+        "speedup_vs_sequential_f64": forms["f16r"]["solves_per_s"] / (len(trace) / seq_dt),
+        "accuracy": "velocity L2 of each served result against the same request solved in FP64 "
+                    "(same step count when both stop on the cap; else each at its own end)"})
     return head
 
 
-def _run_to_steady(clbm, prob, dtype, tol, max_steps, plateau=20, chunk=1000):
-    with clbm.Lattice(**prob.kwargs(), dtype=dtype, check_interval=100) as lat:
+def run_serve_steady(args):
+    """Serving to steady state: a scaled trace whose requests converge within
+    minutes (48 requests, Poisson 20/s, cavities L ~ U{16..48}, channels
+    8 x U{16..64} x 8, Re ~ U[50, 400], n ~ U[0.4, 1.6]), run to residual
+    1e-7 with residual checks every 4000 steps (a per-step rate; the long
+    interval puts the F16R form's rounding floor below the tolerance), in
+    every form and by sequential FP64 on the same requests."""
+    import torch  # noqa: F401  (CUDA context on the chosen device)
+    from paper_1908_05396_gb300 import build, workloads as wl
+    build.build()
+    from paper_1908_05396_gb300 import clbm
+    trace = wl.serving_trace(count=args.serve_requests, seed=0, rate=20.0, cavity_L=(16, 48),
+                             channel_H=(16, 64), Re_range=(50.0, 400.0))
+    wk = (f"{len(trace)} requests, Poisson 20/s (seed 0), half cavities L~U{{16..48}}, half "
+          "channels 8xU{16..64}x8, Re~U[50,400], n~U[0.4,1.6]")
+    out = _serving_bench(clbm, trace, 1e-7, 400_000, 20, 4000, wk,
+                         bars={"f16r": 2e-3, "f16s": 2e-3, "f32": 1e-4})
+    print(json.dumps({"metric": "served solves/s, p50/p99, to steady state", "serving": out}))
+    return 0
+
+
+def _run_to_steady(clbm, prob, dtype, tol, max_steps, plateau=20, chunk=1000, check=100,
+                   progress=None):
+    """Step a lattice until R <= tol, a residual plateau (no 10 % drop over
+    `plateau` reads, one per chunk), divergence or max_steps."""
+    with clbm.Lattice(**prob.kwargs(), dtype=dtype, check_interval=check) as lat:
         lat.autotune(5)
         best, since, steps, R, status = float("inf"), 0, 0, float("inf"), "max_steps"
         t0 = time.perf_counter()
@@ -683,6 +702,9 @@ def _run_to_steady(clbm, prob, dtype, tol, max_steps, plateau=20, chunk=1000):
             lat.step(chunk)
             steps += chunk
             R, rc = lat.residual()
+            if progress and (steps // chunk) % progress == 0:
+                print(f"[{dtype}] step {steps} R {R:.3e} {time.perf_counter() - t0:.0f} s",
+                      file=sys.stderr, flush=True)
             if rc != 0:
                 status = "diverged"
                 break
@@ -795,26 +817,37 @@ def run_stability(args):
 
 def run_precision_steady(args):
     """The precision configuration as written: the 256^3 cavity (Re 1000,
-    n 0.8, U 0.05) run to steady state (residual 1e-8) in FP32, and the F16R
-    and F16S forms run until they converge or their residual stops falling.
-    An FP64 run to steady state at 256^3 takes hours (the FP64 form is ALU
-    bound), so FP32 stands in for it: at 64^3 the two differ by 1.6e-7."""
+    n 0.8, U 0.05) run from rest to steady state (residual 1e-8) in the FP64
+    form, which is the reference (its parity with the oracle is tested at
+    1000 steps), and in the FP32, F16R and F16S forms, which run to the same
+    residual or until it stops falling (20 reads without a 10 % drop).  The
+    residual is checked over intervals of 2000 steps (R is a rate per step,
+    so the tolerance keeps its meaning; the longer interval lowers the
+    residual floor that the FP16 forms' rounding sets).  The velocity L2
+    error of each form against FP64 at its own end is reported."""
     import numpy as np
     import torch  # noqa: F401  (CUDA context on the chosen device)
     from paper_1908_05396_gb300 import build, workloads as wl
     build.build()
     from paper_1908_05396_gb300 import clbm
     prob = wl.cavity(256, 1000.0, 0.8)
-    res = {dt: _run_to_steady(clbm, prob, dt, 1e-8, args.precision_cap, chunk=2000)
-           for dt in ("f32", "f16r", "f16s")}
-    ref = res["f32"][0]
+    forms = args.precision_forms
+    res = {}
+    for dt in forms:
+        res[dt] = _run_to_steady(clbm, prob, dt, 1e-8, args.precision_cap, chunk=2000,
+                                 check=2000, progress=10)
+        print(json.dumps({"form": dt, **res[dt][1]}), file=sys.stderr, flush=True)
+    ref_form = "f64" if "f64" in res else forms[0]
+    ref = res[ref_form][0]
     nref = float(np.linalg.norm(ref))
     print(json.dumps({
         "metric": "precision at steady state",
-        "case": "cavity 256^3, Re 1000, n 0.8, U 0.05, from rest to R <= 1e-8 "
-                "(FP16 forms: or a residual plateau of 20 checks of 2000 steps)",
+        "case": "cavity 256^3, Re 1000, n 0.8, U 0.05, from rest to R <= 1e-8 (check interval "
+                "2000 steps; FP16 forms: or a residual plateau of 20 reads)",
         "runs": {k: v[1] for k, v in res.items()},
-        "l2_vs_f32": {k: float(np.linalg.norm(res[k][0] - ref)) / nref for k in ("f16r", "f16s")}}))
+        "reference": ref_form,
+        f"l2_vs_{ref_form}": {k: float(np.linalg.norm(res[k][0] - ref)) / nref
+                              for k in res if k != ref_form}}))
     return 0
 
 
@@ -885,15 +918,22 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched and serving measurements")
     ap.add_argument("--batch-steps", type=int, default=500)
-    ap.add_argument("--serve-requests", type=int, default=48)
-    ap.add_argument("--serve-seq", type=int, default=8)
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="requests of the serving trace (configured sizes; --serve-steady: scaled)")
+    ap.add_argument("--serve-cap", type=int, default=4000,
+                    help="step cap of each served request in the default run")
+    ap.add_argument("--serve-steady", action="store_true",
+                    help="serving to steady state on a scaled trace, against sequential FP64")
     ap.add_argument("--precision", action="store_true",
                     help="velocity error of the FP32 / F16S forms against FP64")
     ap.add_argument("--precision-steps", type=int, default=2000)
     ap.add_argument("--precision-steady", action="store_true",
-                    help="the 256^3 precision cavity run to steady state (FP32, F16R, F16S)")
+                    help="the 256^3 precision cavity run to steady state (FP64, FP32, F16R, F16S)")
     ap.add_argument("--precision-cap", type=int, default=600_000,
                     help="step cap of each --precision-steady run")
+    ap.add_argument("--precision-forms", nargs="*", default=["f64", "f32", "f16r", "f16s"],
+                    choices=["f64", "f32", "f16r", "f16s"],
+                    help="forms of --precision-steady, the first the reference unless FP64 runs")
     ap.add_argument("--profile-batch", action="store_true",
                     help="time only the batch of 64 cavities (profiling case)")
     ap.add_argument("--batch-bps", type=int, default=4,
@@ -933,6 +973,10 @@ def main():
         return run_precision(args)
     if args.precision_steady:
         return run_precision_steady(args)
+    if args.serve_steady:
+        if args.serve_requests == 32:
+            args.serve_requests = 48
+        return run_serve_steady(args)
     if args.stability:
         return run_stability(args)
     if args.profile:

@@ -256,14 +256,15 @@ __device__ __forceinline__ void pdl_enter() {
 }
 
 // Launch a kernel whose threads start with pdl_enter(), with the programmatic
-// stream-serialisation attribute (compiled out with -DCLBM_NO_PDL).
+// stream-serialisation attribute (compiled out with -DCLBM_NO_PDL) and
+// `smem` bytes of dynamic shared memory.
 template <typename... KArgs, typename... Args>
-inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
-                              const Args&... args) {
+inline cudaError_t pdl_launch_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                   cudaStream_t st, const Args&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -275,6 +276,11 @@ inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, c
   cfg.numAttrs = 1;
 #endif
   return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                              const Args&... args) {
+  return pdl_launch_smem(kernel, grid, block, 0, st, args...);
 }
 
 // One time step.  Warps off the y and z faces load all 19 upwind values

@@ -129,14 +129,51 @@ __device__ __forceinline__ void pull_face_ref(const __half* __restrict__ src,
   }
 }
 
+// Shared memory of one block of the step: the reference moments of its
+// nodes and their neighbours, (bx + 2) x (by + 2) nodes in each of the
+// planes z - 1, z, z + 1, decoded to FP32 once per block.
+__host__ __device__ inline size_t ref_stage_bytes(int bx, int by) {
+  return size_t(3) * size_t(bx + 2) * size_t(by + 2) * sizeof(float4);
+}
+
 template <bool FORCE, bool CHECK, bool CAP>
 __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepArgs<__half, float> a,
                                                                     const RefArgs r) {
+  extern __shared__ float4 sref[];
   pdl_enter();
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int bx = int(blockDim.x), by = int(blockDim.y);
+  const int sx = bx + 2, sxy = sx * (by + 2);
+  const int x = blockIdx.x * bx + threadIdx.x;
+  const int y = blockIdx.y * by + threadIdx.y;
   const int z = a.zrev ? a.nz - 1 - int(blockIdx.z) : int(blockIdx.z);  // as step_kernel
   const bool active = x < a.nx && y < a.ny;
+  // Blocks off the z faces stage the references that their interior nodes
+  // read (every upwind neighbour lies in the staged box), instead of one
+  // 8-byte load and conversion per direction and node.  Nodes outside the
+  // lattice are staged as zeros and never read: their readers are face
+  // nodes, which take pull_face_ref.
+  const bool zin = z > 0 && z < a.nz - 1;  // block-uniform
+  if (zin) {
+    const int x0 = int(blockIdx.x) * bx - 1, y0 = int(blockIdx.y) * by - 1;
+    for (int ky = threadIdx.y; ky < by + 2; ky += by) {
+      const int gy = y0 + ky;
+      for (int kx = threadIdx.x; kx < sx; kx += bx) {
+        const int gx = x0 + kx;
+        const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
+        const int gi = (z - 1) * a.plane + gy * a.pitch + gx;
+#pragma unroll
+        for (int kz = 0; kz < 3; ++kz) {
+          float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          if (in) {
+            const Ref4 t = ref_load(r.ref_src + gi + kz * a.plane);
+            v = make_float4(t.dr, t.vx, t.vy, t.vz);
+          }
+          sref[kz * sxy + ky * sx + kx] = v;
+        }
+      }
+    }
+    __syncthreads();
+  }
   if (!CHECK && !active) return;
   const float rho0 = a.C.rho0;
   double du2 = 0.0, uu = 0.0, dr = 0.0;
@@ -144,10 +181,13 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
   if (active) {
     const int i = z * a.plane + y * a.pitch + x;
     float d[Q];
-    if (y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1) {
+    if (y > 0 && y < a.ny - 1 && zin) {
+      const float4* c = sref + sxy + (int(threadIdx.y) + 1) * sx + (int(threadIdx.x) + 1);
 #pragma unroll
-      for (int q = 0; q < Q; ++q)
-        d[q] = dec16(a.srcq[q][i]) + ref_term(q, ref_load(r.refq[q] + i), rho0);
+      for (int q = 0; q < Q; ++q) {
+        const float4 t = c[-cz(q) * sxy - cy(q) * sx - cx(q)];
+        d[q] = dec16(a.srcq[q][i]) + ref_term(q, Ref4{t.x, t.y, t.z, t.w}, rho0);
+      }
       if (x == 0 || x == a.nx - 1) {
         const int kl = a.facebits & 3, kr = (a.facebits >> 2) & 3;
 #pragma unroll
@@ -399,10 +439,11 @@ cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, vo
   const bool cap = (npt & 4) != 0;
   dim3 grid((g.nx + block.x - 1) / block.x, (g.ny + block.y - 1) / block.y, g.nz);
   cudaError_t e_ = cudaSuccess;
+  const size_t smem = ref_stage_bytes(int(block.x), int(block.y));
 #define CLBM_REF_LAUNCH(F, C_)                                                                  \
   do {                                                                                         \
-    if (cap) e_ = pdl_launch(step_ref_kernel<F, C_, true>, grid, block, st, a, r);            \
-    else e_ = pdl_launch(step_ref_kernel<F, C_, false>, grid, block, st, a, r);               \
+    if (cap) e_ = pdl_launch_smem(step_ref_kernel<F, C_, true>, grid, block, smem, st, a, r);  \
+    else e_ = pdl_launch_smem(step_ref_kernel<F, C_, false>, grid, block, smem, st, a, r);     \
   } while (0)
   if (P.has_force) {
     if (check) CLBM_REF_LAUNCH(true, true);
