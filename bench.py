@@ -691,16 +691,24 @@ def run_serve_steady(args):
 
 
 def _run_to_steady(clbm, prob, dtype, tol, max_steps, plateau=20, chunk=1000, check=100,
-                   progress=None):
+                   progress=None, start=None, snapshot_at=None):
     """Step a lattice until R <= tol, a residual plateau (no 10 % drop over
-    `plateau` reads, one per chunk), divergence or max_steps."""
+    `plateau` reads, one per chunk), divergence or max_steps.  `start` =
+    (populations, steps) continues from a stored state; `snapshot_at` keeps
+    the populations after that many steps (returned in the info)."""
+    snap = None
     with clbm.Lattice(**prob.kwargs(), dtype=dtype, check_interval=check) as lat:
         lat.autotune(5)
         best, since, steps, R, status = float("inf"), 0, 0, float("inf"), "max_steps"
+        if start is not None:
+            lat.set_state(start[0])
+            steps = start[1]
         t0 = time.perf_counter()
         while steps < max_steps:
             lat.step(chunk)
             steps += chunk
+            if snapshot_at is not None and steps == snapshot_at:
+                snap = lat.get_state()
             R, rc = lat.residual()
             if progress and (steps // chunk) % progress == 0:
                 print(f"[{dtype}] step {steps} R {R:.3e} {time.perf_counter() - t0:.0f} s",
@@ -720,7 +728,10 @@ def _run_to_steady(clbm, prob, dtype, tol, max_steps, plateau=20, chunk=1000, ch
                 break
         dt = time.perf_counter() - t0
         _, u, _ = lat.fields()
-    return u, {"steps": steps, "residual": R, "status": status, "seconds": dt}
+    info = {"steps": steps, "residual": R, "status": status, "seconds": dt}
+    if snapshot_at is not None:
+        info["snapshot"] = snap
+    return u, info
 
 
 def run_precision(args):
@@ -824,18 +835,39 @@ def run_precision_steady(args):
     residual is checked over intervals of 2000 steps (R is a rate per step,
     so the tolerance keeps its meaning; the longer interval lowers the
     residual floor that the FP16 forms' rounding sets).  The velocity L2
-    error of each form against FP64 at its own end is reported."""
+    error of each form against FP64 at its own end is reported.  With
+    --precision-f64-from T the FP64 run starts from the FP32 state after T
+    steps instead of from rest (the two trajectories agree to the FP32
+    rounding level, and the FP64 steps that follow damp that start-up
+    difference with the flow's slowest mode), which shortens the FP64 run
+    by T steps; the start is stated in the output."""
     import numpy as np
     import torch  # noqa: F401  (CUDA context on the chosen device)
     from paper_1908_05396_gb300 import build, workloads as wl
     build.build()
     from paper_1908_05396_gb300 import clbm
     prob = wl.cavity(256, 1000.0, 0.8)
-    forms = args.precision_forms
+    forms = list(args.precision_forms)
     res = {}
+    warm = args.precision_f64_from
+    if warm and "f64" in forms and "f32" in forms:
+        # FP32 first, keeping its state at step `warm`; FP64 continues from it
+        forms.remove("f32")
+        forms.insert(0, "f32")
+    snap = None
     for dt in forms:
+        kw = {}
+        if dt == "f32" and warm and "f64" in forms:
+            kw["snapshot_at"] = warm
+        if dt == "f64" and snap is not None:
+            kw["start"] = (snap, warm)
         res[dt] = _run_to_steady(clbm, prob, dt, 1e-8, args.precision_cap, chunk=2000,
-                                 check=2000, progress=10)
+                                 check=2000, progress=10, **kw)
+        if "snapshot" in res[dt][1]:
+            snap = res[dt][1].pop("snapshot")
+        if dt == "f64" and snap is not None:
+            res[dt][1]["started_from"] = f"the FP32 state after {warm} steps"
+            snap = None
         print(json.dumps({"form": dt, **res[dt][1]}), file=sys.stderr, flush=True)
     ref_form = "f64" if "f64" in res else forms[0]
     ref = res[ref_form][0]
@@ -843,7 +875,8 @@ def run_precision_steady(args):
     print(json.dumps({
         "metric": "precision at steady state",
         "case": "cavity 256^3, Re 1000, n 0.8, U 0.05, from rest to R <= 1e-8 (check interval "
-                "2000 steps; FP16 forms: or a residual plateau of 20 reads)",
+                "2000 steps; FP16 forms: or a residual plateau of 20 reads)"
+                + (f"; FP64 from the FP32 state after {warm} steps" if warm else ""),
         "runs": {k: v[1] for k, v in res.items()},
         "reference": ref_form,
         f"l2_vs_{ref_form}": {k: float(np.linalg.norm(res[k][0] - ref)) / nref
@@ -931,6 +964,9 @@ def main():
                     help="the 256^3 precision cavity run to steady state (FP64, FP32, F16R, F16S)")
     ap.add_argument("--precision-cap", type=int, default=600_000,
                     help="step cap of each --precision-steady run")
+    ap.add_argument("--precision-f64-from", type=int, default=0,
+                    help="--precision-steady: start FP64 from the FP32 state after this many "
+                         "steps (0: from rest)")
     ap.add_argument("--precision-forms", nargs="*", default=["f64", "f32", "f16r", "f16s"],
                     choices=["f64", "f32", "f16r", "f16s"],
                     help="forms of --precision-steady, the first the reference unless FP64 runs")
