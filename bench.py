@@ -977,7 +977,7 @@ def main():
     ap.add_argument("--launch", type=int, nargs=3, default=None,
                     metavar=("BX", "BY", "NPT"), help="profiling case: fixed launch shape")
     ap.add_argument("--profile", nargs="?", const="f32", default=None,
-                    choices=["f64", "f32", "f16s"],
+                    choices=["f64", "f32", "f16s", "f16r"],
                     help="time only the steps of the n=0.5 cavity in one storage form "
                          "(profiling case)")
     ap.add_argument("--stability", action="store_true",

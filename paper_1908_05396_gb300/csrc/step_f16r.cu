@@ -7,7 +7,7 @@
 //     r_q = w_q [ drho + e_q . v ],  v = 3 (rho0 + drho) u  (reference values),
 // which removes the rest value and the first-order (velocity) part of the
 // equilibrium, the largest parts of f~, before FP16 rounding (stochastic in
-// the step kernels, see enc16_sr).  A reader
+// the step kernels, see enc16_sr2).  A reader
 // decodes with the reference of the node that wrote the value: the upwind
 // neighbour for a streamed value, itself for a bounced one.  Both sides use
 // the reference exactly as stored (rounded to FP16), so the encoding is
@@ -56,16 +56,12 @@ __device__ __forceinline__ __half enc16(float v) { return __float2half_rn(v * fl
 // Stochastic rounding of the stores: a value is rounded up in magnitude with
 // probability equal to the fraction of an FP16 ulp it carries, so increments
 // far below one ulp (a weak body force, a slow transient) survive on average
-// instead of being rounded away every step.  FP16 keeps 10 of FP32's 23
-// mantissa bits: a uniform 13-bit integer is added to the FP32 bit pattern and
-// the 13 low bits are cleared, which leaves a value FP16 holds exactly
-// (magnitudes below the FP16 normal range lose their last bits toward zero).
-// The random bits depend only on the node index, the direction and the
-// lattice's own step count, so a lattice gives the same result alone and in
-// a batch: one integer hash of (node, step) (the finaliser of MurmurHash3),
-// then one step per direction of a 32-bit linear congruential generator with
-// the multiplier and increment of PCG (O'Neill, 2014), whose top 13 bits are
-// used.
+// instead of being rounded away every step.  The random bits depend only on
+// the node index, the direction pair and the lattice's own step count, so a
+// lattice gives the same result alone and in a batch: one integer hash of
+// (node, step) (the finaliser of MurmurHash3), then one step per pair of
+// directions of a 32-bit linear congruential generator with the multiplier
+// and increment of PCG (O'Neill, 2014).
 __device__ __forceinline__ uint32_t sr_seed(uint32_t node, uint32_t step) {
   uint32_t h = node ^ (step * 0x9E3779B9u);
   h ^= h >> 16;
@@ -75,11 +71,36 @@ __device__ __forceinline__ uint32_t sr_seed(uint32_t node, uint32_t step) {
   h ^= h >> 16;
   return h;
 }
-__device__ __forceinline__ __half enc16_sr(float v, uint32_t& state) {
+
+// Two values at once with the GB300's stochastic-rounding conversion
+// (cvt.rs.f16x2.f32: each value rounded up in magnitude with the probability
+// of the fraction of an FP16 ulp it carries, using the random bits given).
+// One 32-bit step of the generator above feeds both; hi receives a, lo b.
+__device__ __forceinline__ void enc16_sr2(float a, float b, uint32_t& state, __half& hi,
+                                          __half& lo) {
   state = state * 747796405u + 2891336453u;
-  uint32_t b = __float_as_uint(v * float(F16_SCALE));
-  b = (b + (state >> 19)) & 0xFFFFE000u;
-  return __float2half_rz(__uint_as_float(b));
+  uint32_t d;
+  asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;"
+      : "=r"(d)
+      : "f"(a * float(F16_SCALE)), "f"(b * float(F16_SCALE)), "r"(state));
+  hi = __ushort_as_half(static_cast<unsigned short>(d >> 16));
+  lo = __ushort_as_half(static_cast<unsigned short>(d & 0xFFFFu));
+}
+
+// Store the 19 post-collision remainders of node i with stochastic rounding,
+// two directions per conversion.
+template <typename Dst>
+__device__ __forceinline__ void store_sr(Dst&& dst_q, const float (&d)[Q], const Ref4& rr,
+                                         float rho0, uint32_t state) {
+#pragma unroll
+  for (int q = 0; q < Q; q += 2) {
+    const float a = d[q] - ref_term(q, rr, rho0);
+    const float b = q + 1 < Q ? d[q + 1] - ref_term(q + 1 < Q ? q + 1 : q, rr, rho0) : 0.0f;
+    __half hi, lo;
+    enc16_sr2(a, b, state, hi, lo);
+    dst_q(q) = hi;
+    if (q + 1 < Q) dst_q(q + 1) = lo;
+  }
 }
 
 struct RefArgs {
@@ -214,9 +235,8 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
     collide<float, FORCE>(a.C, d, o);
     Ref4 rr;
     r.ref_dst[i] = ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rho0, rr);
-    uint32_t rs = sr_seed(uint32_t(i), r.step);
-#pragma unroll
-    for (int q = 0; q < Q; ++q) a.dstq[q][i] = enc16_sr(d[q] - ref_term(q, rr, rho0), rs);
+    store_sr([&](int q) -> __half& { return a.dstq[q][i]; }, d, rr, rho0,
+             sr_seed(uint32_t(i), r.step));
     if (CHECK) {
       float* up = reinterpret_cast<float*>(a.cb.uprev);
       const int64_t nst = int64_t(a.plane) * a.nz;
@@ -401,9 +421,7 @@ __device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y
   collide<float, FORCE>(L.C, d, o);
   Ref4 rr;
   rd[i] = ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rho0, rr);
-  uint32_t rst = sr_seed(uint32_t(i), step);
-#pragma unroll
-  for (int q = 0; q < Q; ++q) dst[q * qs + i] = enc16_sr(d[q] - ref_term(q, rr, rho0), rst);
+  store_sr([&](int q) -> __half& { return dst[q * qs + i]; }, d, rr, rho0, sr_seed(uint32_t(i), step));
 }
 
 cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, void* ref_dst,
