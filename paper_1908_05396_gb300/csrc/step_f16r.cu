@@ -380,9 +380,34 @@ void lid_table(const Geom& g, float* out) {
 
 // One node of the batched step in the F16R form: the same pull, references
 // and collision as step_ref_kernel.
+__device__ void ref_stage_batch(const LatDesc<float>& L, int parity, int x0, int y0, int z,
+                                int tw, int th, int lin, int twl, float4* sref) {
+  const uint2* rs = static_cast<const uint2*>(L.ref[parity]);
+  const int sx = tw + 2, sxy = sx * (th + 2);
+  const int lx = lin & (tw - 1), ly = lin >> twl;
+  for (int ky = ly; ky < th + 2; ky += th) {
+    const int gy = y0 - 1 + ky;
+    for (int kx = lx; kx < sx; kx += tw) {
+      const int gx = x0 - 1 + kx;
+      const bool in = gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny;
+      const int gi = (z - 1) * L.plane + gy * L.pitch + gx;
+#pragma unroll
+      for (int kz = 0; kz < 3; ++kz) {
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (in) {
+          const Ref4 t = ref_load(rs + gi + kz * L.plane);
+          v = make_float4(t.dr, t.vx, t.vy, t.vz);
+        }
+        sref[kz * sxy + ky * sx + kx] = v;
+      }
+    }
+  }
+}
+
 template <bool FORCE>
 __device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y, int z,
-                               unsigned step, NodeOut<float>& o) {
+                               unsigned step, NodeOut<float>& o, const float4* sref, int sx,
+                               int sxy) {
   const __half* src = static_cast<const __half*>(L.buf[parity]);
   __half* dst = static_cast<__half*>(const_cast<void*>(L.buf[parity ^ 1]));
   const uint2* rs = static_cast<const uint2*>(L.ref[parity]);
@@ -395,7 +420,8 @@ __device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int j = i - (cz(q) * plane + cy(q) * pitch + cx(q));
-      d[q] = dec16(src[q * qs + j]) + ref_term(q, ref_load(rs + j), rho0);
+      const float4 t = sref[-cz(q) * sxy - cy(q) * sx - cx(q)];
+      d[q] = dec16(src[q * qs + j]) + ref_term(q, Ref4{t.x, t.y, t.z, t.w}, rho0);
     }
     if (x == 0 || x == L.nx - 1) {
       const int kl = L.facebits & 3, kr = (L.facebits >> 2) & 3;
