@@ -372,6 +372,21 @@ int clbm_collide_nodes(clbm_dtype dtype, double K, double n,
                        double nu_max, const double* f_in, double* f_out,
                        double* rho, double* u, double* gamma_dot, int64_t M);
 
+/* The local relaxation rate omega_nu (Eq. localvarationsrelaxationtimes with
+ * the power law of Eq. 6) and |gamma_dot| (Eqs. strainratetensor,
+ * shearrateexpression) of M nodes, solved on the current device exactly as
+ * the collision of storage form dtype solves them (FP64 for CLBM_F64, FP32
+ * for the other forms), with omega_9..18 = 1 and the viscosity clamped to
+ * [nu_min, nu_max] (0 -> 5e-4, 10).
+ *   rho:   M densities (host, FP64);
+ *   m:     host array of 6 x M non-equilibrium second moments
+ *          m^(1)_4..m^(1)_9 of Sec. 3.2, [moment][node];
+ *   omega, gamma_dot: M outputs each (host; gamma_dot may be NULL).
+ * Synchronous.  Errors: CLBM_ERR_ARG, CLBM_ERR_OOM, CLBM_ERR_CUDA. */
+int clbm_omega_nodes(clbm_dtype dtype, double K, double n, double nu_min, double nu_max,
+                     const double* rho, const double* m, double* omega, double* gamma_dot,
+                     int64_t M);
+
 /* Fused multiply-add throughput of the current device, in FLOP/s (two per
  * FMA), for dtype CLBM_F64 or CLBM_F32: a measurement utility with no
  * counterpart in the paper.  It gives the arithmetic ceiling of a step form

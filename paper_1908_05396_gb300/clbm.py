@@ -85,7 +85,10 @@ def lib():
             L.clbm_set_rates.argtypes = [_H, _D]
             L.clbm_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, ctypes.c_void_p]
             L.clbm_probe_fma_rate.argtypes = [ctypes.c_int, _D]
-            for name in ("clbm_probe_fma_rate", "clbm_autotune", "clbm_set_launch", "clbm_set_rates", "clbm_set_allocator",
+            L.clbm_omega_nodes.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, _D, _D, _D, _D,
+                                           ctypes.c_int64]
+            for name in ("clbm_probe_fma_rate", "clbm_omega_nodes", "clbm_autotune", "clbm_set_launch", "clbm_set_rates", "clbm_set_allocator",
                          "clbm_create", "clbm_step", "clbm_fields", "clbm_fields_device",
                          "clbm_residual", "clbm_mass", "clbm_get_state", "clbm_set_state",
                          "clbm_steps_done", "clbm_sync", "clbm_destroy", "clbm_collide_nodes"):
@@ -327,6 +330,23 @@ def step_noalloc(nx, ny, nz, face, K, n, U_lid, body_force, dtype, src, dst, u_p
     return L.clbm_step_noalloc(ctypes.byref(d), float(K), float(n), _vec3(U_lid), _vec3(body_force),
                                code, ctypes.c_void_p(src), ctypes.c_void_p(dst),
                                ctypes.c_void_p(u_prev), ctypes.c_void_p(stats))
+
+
+def omega_nodes(rho: np.ndarray, m: np.ndarray, K: float, n: float, dtype="f64", nu_min=0.0,
+                nu_max=0.0):
+    """omega_nu and |gamma_dot| of M nodes from rho (M,) and the non-equilibrium
+    moments m^(1)_4..9 given as an array (6, M) (``clbm_omega_nodes``)."""
+    L = lib()
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    M = rho.shape[0]
+    assert m.shape == (6, M)
+    omega = np.empty(M)
+    gd = np.empty(M)
+    code = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    _check(L.clbm_omega_nodes(code, float(K), float(n), float(nu_min), float(nu_max), _dp(rho),
+                              _dp(m), _dp(omega), _dp(gd), M))
+    return omega, gd
 
 
 def probe_fma_rate(dtype="f64") -> float:

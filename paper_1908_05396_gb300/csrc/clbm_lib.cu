@@ -676,4 +676,39 @@ int clbm_collide_nodes(clbm_dtype dtype, double K, double n, const double body_f
   return CLBM_OK;
 }
 
+int clbm_omega_nodes(clbm_dtype dtype, double K, double n, double nu_min, double nu_max,
+                     const double* rho, const double* m, double* omega, double* gamma_dot,
+                     int64_t M) {
+  if (!rho || !m || !omega || M <= 0) return fail(nullptr, CLBM_ERR_ARG, "bad node arrays");
+  if (dtype != CLBM_F64 && dtype != CLBM_F32 && dtype != CLBM_F16S && dtype != CLBM_F16R)
+    return fail(nullptr, CLBM_ERR_ARG, "unknown dtype");
+  nu_min = nu_min > 0 ? nu_min : 5e-4;
+  nu_max = nu_max > 0 ? nu_max : 10.0;
+  std::string why;
+  if (!check_phys(K, n, nu_min, nu_max, why)) return fail(nullptr, CLBM_ERR_ARG, why);
+  PhysParams P{};
+  fill_params(P, K, n, nullptr, 1.0, nu_min, nu_max, dtype);
+  double* dev = nullptr;
+  const size_t bytes = size_t(M) * (1 + 6 + 1 + 1) * sizeof(double);
+  cudaError_t e = cudaMalloc(&dev, bytes);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaMalloc");
+  double* drho = dev;
+  double* dm = drho + M;
+  double* dw = dm + 6 * M;
+  double* dgd = dw + M;
+  e = cudaMemcpy(drho, rho, M * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dm, m, 6 * M * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    // every FP32-math form solves in FP32 with the same code
+    e = dtype == CLBM_F64 ? launch_omega_nodes_f64(P, drho, dm, dw, dgd, M, 0)
+                          : launch_omega_nodes_f32(P, drho, dm, dw, dgd, M, 0);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(omega, dw, M * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && gamma_dot)
+    e = cudaMemcpy(gamma_dot, dgd, M * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "clbm_omega_nodes");
+  return CLBM_OK;
+}
+
 }  // extern "C"

@@ -478,6 +478,19 @@ constexpr bool add_K_g_source() {
 static_assert(add_K_g_is_K(), "the additive back-transform must add the columns of K");
 static_assert(add_K_g_source(), "the additive back-transform must add the body-force source");
 
+// gamma_dot^2 = omega^2 A + B from Eq. strainratetensor (bulk rate omega_9)
+// and Eq. shearrateexpression, for the non-equilibrium moments m^(1)_4..9
+// (Sec. 3.2): with q = 1/(2 rho), the traceless part gives
+// A = 12 q^2 [m7^2 - m7 m8 + m8^2 + 3 (m4^2 + m5^2 + m6^2)] and the
+// isotropic part B = 6 omega_9^2 q^2 m9^2.
+template <typename R, typename T>
+__device__ __forceinline__ void strain_AB(const CollideConst<T>& C, R rinv, R m4, R m5, R m6,
+                                          R m7, R m8, R m9, R& A, R& B) {
+  const R q2 = R(0.25) * rinv * rinv;
+  A = R(12) * q2 * (m7 * m7 - m7 * m8 + m8 * m8 + R(3) * (m4 * m4 + m5 * m5 + m6 * m6));
+  B = R(C.cB) * q2 * m9 * m9;  // 6 omega_9^2 q^2 m9^2
+}
+
 // Collide one node.  d[19] holds the pre-collision deviations on entry and
 // the post-collision deviations f~ - w rho0 on return.
 // PAIR_OUT selects how the populations are written back: rebuilt from the
@@ -536,13 +549,8 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
   const R m8 = (Dxx - Dzz) - rho * (ux2 - uz2);
   const R m9 = (Dxx + Dyy + Dzz) - drho - rho * (ux2 + uy2 + uz2);
 
-  // gamma_dot^2 = omega^2 A + B from Eq. strainratetensor (bulk rate
-  // omega_9): with q = 1/(2 rho), the traceless part gives
-  // A = 12 q^2 [m7^2 - m7 m8 + m8^2 + 3 (m4^2 + m5^2 + m6^2)] and the
-  // isotropic part B = 6 omega_9^2 q^2 m9^2.
-  const R q2 = R(0.25) * rinv * rinv;
-  const R A = R(12) * q2 * (m7 * m7 - m7 * m8 + m8 * m8 + R(3) * (m4 * m4 + m5 * m5 + m6 * m6));
-  const R B = R(C.cB) * q2 * m9 * m9;   // 6 omega_9^2 q^2 m9^2
+  R A, B;
+  strain_AB(C, rinv, m4, m5, m6, m7, m8, m9, A, B);
   R gd;
   const R w = omega_nu(C, rho, rinv, A, B, &gd);
 

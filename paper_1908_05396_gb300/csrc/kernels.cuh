@@ -500,6 +500,27 @@ __global__ void collide_nodes_kernel(PhysParams P, const double* __restrict__ fi
   if (gd) gd[k] = double(o.gamma_dot);
 }
 
+// The local relaxation rate omega_nu and |gamma_dot| of M nodes from their
+// density and non-equilibrium moments m^(1)_4..9 ([6][node], FP64), solved
+// in the math precision R exactly as the collision does.
+template <typename R>
+__global__ void omega_nodes_kernel(PhysParams P, const double* __restrict__ rho_in,
+                                   const double* __restrict__ m, double* omega, double* gd,
+                                   int64_t M) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= M) return;
+  const CollideConst<R> C = make_const<R>(P);
+  const R rho = R(rho_in[k]);
+  const R rinv = rrcp<R>(rho);
+  R A, B;
+  strain_AB(C, rinv, R(m[k]), R(m[M + k]), R(m[2 * M + k]), R(m[3 * M + k]), R(m[4 * M + k]),
+            R(m[5 * M + k]), A, B);
+  R g;
+  const R w = omega_nu(C, rho, rinv, A, B, &g);
+  omega[k] = double(w);
+  if (gd) gd[k] = double(g);
+}
+
 // Stored populations <-> plain FP64 f in the unpadded layout [q][z][y][x].
 template <typename S>
 __global__ void export_kernel(const S* __restrict__ src, Geom g, double rho0,
@@ -635,6 +656,14 @@ cudaError_t launch_collide_nodes_t(const PhysParams& P, const double* fin, doubl
   return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_omega_nodes_t(const PhysParams& P, const double* rho, const double* m,
+                                 double* omega, double* gd, int64_t M, cudaStream_t st) {
+  const int b = 128;
+  omega_nodes_kernel<R><<<unsigned((M + b - 1) / b), b, 0, st>>>(P, rho, m, omega, gd, M);
+  return cudaGetLastError();
+}
+
 template <typename S>
 cudaError_t launch_export_t(const void* src, const Geom& g, double rho0, double inv_scale,
                             double* out, cudaStream_t st) {
@@ -677,6 +706,11 @@ cudaError_t launch_import_t(const double* in, const Geom& g, double rho0, double
   cudaError_t launch_export_##SUFFIX(const void* src, const Geom& g, double rho0,             \
                                      double inv_scale, double* out, cudaStream_t st) {        \
     return launch_export_t<S>(src, g, rho0, inv_scale, out, st);                              \
+  }                                                                                           \
+  cudaError_t launch_omega_nodes_##SUFFIX(const PhysParams& P, const double* rho,             \
+                                          const double* m, double* omega, double* gd,         \
+                                          int64_t M, cudaStream_t st) {                       \
+    return launch_omega_nodes_t<R>(P, rho, m, omega, gd, M, st);                              \
   }                                                                                           \
   cudaError_t launch_import_##SUFFIX(const double* in, const Geom& g, double rho0,            \
                                      double inv_scale, void* dst, cudaStream_t st) {          \

@@ -88,6 +88,9 @@ __host__ __device__ constexpr int tma_by(int v) {
                                             int64_t M, cudaStream_t st);                      \
   cudaError_t launch_export_##SUFFIX(const void* src, const Geom& g, double rho0,             \
                                      double inv_scale, double* out, cudaStream_t st);         \
+  cudaError_t launch_omega_nodes_##SUFFIX(const PhysParams& P, const double* rho,             \
+                                          const double* m, double* omega, double* gd,         \
+                                          int64_t M, cudaStream_t st);                        \
   cudaError_t launch_import_##SUFFIX(const double* in, const Geom& g, double rho0,            \
                                      double inv_scale, void* dst, cudaStream_t st);
 

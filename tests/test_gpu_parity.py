@@ -556,3 +556,39 @@ def test_unit_rates_change_nothing_and_bad_rates_are_rejected(clbm):
             batch.add(b)
             with pytest.raises(clbm.CLBMError):
                 b.set_rates([1.2] * 10)
+
+
+@pytest.mark.parametrize("dtype,rtol", [("f64", 1e-13), ("f32", 2e-5)])
+def test_omega_solve_vs_oracle_over_shear_range(clbm, oracle, dtype, rtol):
+    # The local relaxation rate (Eq. localvarationsrelaxationtimes with the
+    # power law of Eq. 6, clamped viscosity: reading c6) from vanishing to
+    # high shear, solved on the GPU as each form's collision solves it,
+    # against the oracle's bisection node by node.  The non-equilibrium
+    # moments span 15 decades, so the sweep covers both clamps, the
+    # transitions onto them and the unclamped range, with and without a bulk
+    # part; the FP32 forms solve in FP32 throughout (base-2 logarithms).
+    rng = np.random.default_rng(31)
+    lo_w, hi_w = 1.0 / (3 * 10.0 + 0.5), 1.0 / (3 * 5e-4 + 0.5)
+    errs, gerrs, kinds = [], [], {"nu_max": 0, "nu_min": 0, "free": 0}
+    for n in (0.4, 0.6, 1.0, 1.3, 1.6):
+        for K in (1e-5, 1e-3, 0.1, 2.0):
+            M = 300
+            s = 10.0 ** rng.uniform(-16, -1, M)
+            rho = rng.uniform(0.97, 1.03, M)
+            m = s * rng.uniform(-1, 1, (6, M))
+            m[5] *= rng.choice([0.0, 0.1, 10.0], M)      # bulk part m9: none, small, large
+            w, gd = clbm.omega_nodes(rho, m, K, n, dtype)
+            p = oracle.Params(K=K, n=n)
+            for k in range(M):
+                mm = np.zeros(10)
+                mm[4:10] = m[:, k]
+                w_ref, gd_ref = oracle.omega_solve(p, rho[k], mm)
+                errs.append(abs(w[k] - w_ref) / w_ref)
+                if gd_ref > 0:
+                    gerrs.append(abs(gd[k] - gd_ref) / gd_ref)
+                key = ("nu_max" if w_ref <= lo_w * (1 + 1e-12) else
+                       "nu_min" if w_ref >= hi_w * (1 - 1e-12) else "free")
+                kinds[key] += 1
+    assert min(kinds.values()) >= 100, kinds       # both clamps and the free range are hit
+    assert max(errs) <= rtol, max(errs)
+    assert max(gerrs) <= rtol, max(gerrs)
