@@ -169,17 +169,20 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
   const int z = a.zrev ? a.nz - 1 - int(blockIdx.z) : int(blockIdx.z);  // as step_kernel
   const bool active = x < a.nx && y < a.ny;
   // Blocks off the z faces stage the references that their interior nodes
-  // read (every upwind neighbour lies in the staged box), instead of one
-  // 8-byte load and conversion per direction and node.  Nodes outside the
-  // lattice are staged as zeros and never read: their readers are face
-  // nodes, which take pull_face_ref.
+  // read (every upwind neighbour lies in the staged box, the periodic wrap
+  // along x included), instead of one 8-byte load and conversion per
+  // direction and node.  Nodes outside the lattice are staged as zeros and
+  // never read: their readers are y or z face nodes, which take
+  // pull_face_ref, or x face nodes, which bounce back.
   const bool zin = z > 0 && z < a.nz - 1;  // block-uniform
   if (zin) {
     const int x0 = int(blockIdx.x) * bx - 1, y0 = int(blockIdx.y) * by - 1;
+    const bool xper = (a.facebits & 3u) == unsigned(BC_PERIODIC);
     for (int ky = threadIdx.y; ky < by + 2; ky += by) {
       const int gy = y0 + ky;
       for (int kx = threadIdx.x; kx < sx; kx += bx) {
-        const int gx = x0 + kx;
+        int gx = x0 + kx;
+        if (xper) gx = gx == -1 ? a.nx - 1 : gx == a.nx ? 0 : gx;
         const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
         const int gi = (z - 1) * a.plane + gy * a.pitch + gx;
 #pragma unroll
@@ -204,28 +207,31 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
     float d[Q];
     if (y > 0 && y < a.ny - 1 && zin) {
       const float4* c = sref + sxy + (int(threadIdx.y) + 1) * sx + (int(threadIdx.x) + 1);
+      // One load per direction: a lane on an x face takes, for the five
+      // directions that come from outside, the periodic wrap (the upwind
+      // reference is staged wrapped) or the halfway bounce-back from its own
+      // opposite population (decoded with its own reference: the term of
+      // opp(q) is w_q (dr - e_q.v)) plus the lid term.
+      const bool fl = x == 0, fr = x == a.nx - 1;
+      const int kl = a.facebits & 3, kr = (a.facebits >> 2) & 3;
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        const float4 t = c[-cz(q) * sxy - cy(q) * sx - cx(q)];
-        d[q] = dec16(a.srcq[q][i]) + ref_term(q, Ref4{t.x, t.y, t.z, t.w}, rho0);
-      }
-      if (x == 0 || x == a.nx - 1) {
-        const int kl = a.facebits & 3, kr = (a.facebits >> 2) & 3;
-#pragma unroll
-        for (int q = 1; q < Q; ++q) {
-          const bool left = cx(q) == 1 && x == 0, right = cx(q) == -1 && x == a.nx - 1;
-          if (left || right) {
-            const int k = left ? kl : kr;
-            if (k == BC_PERIODIC) {
-              const int j = left ? i + a.nx : i - a.nx;
-              d[q] = dec16(a.srcq[q][j]) + ref_term(q, ref_load(r.refq[q] + j), rho0);
-            } else {
-              d[q] = dec16(a.src[opp(q) * a.qstride + i]) +
-                     ref_term(opp(q), ref_load(r.ref_src + i), rho0) +
-                     (k == BC_LID ? a.lidc[q] : 0.0f);
-            }
+        const __half* pq = a.srcq[q] + i;
+        float4 t = c[-cz(q) * sxy - cy(q) * sx - cx(q)];
+        float sgn = 1.0f, extra = 0.0f;
+        if ((cx(q) == 1 && fl) || (cx(q) == -1 && fr)) {
+          const int k = cx(q) == 1 ? kl : kr;
+          if (k == BC_PERIODIC) {
+            pq += cx(q) == 1 ? a.nx : -a.nx;
+          } else {
+            pq = a.src + int64_t(opp(q)) * a.qstride + i;
+            t = c[0];
+            sgn = -1.0f;
+            extra = k == BC_LID ? a.lidc[q] : 0.0f;
           }
         }
+        const float ev = float(cx(q)) * t.y + float(cy(q)) * t.z + float(cz(q)) * t.w;
+        d[q] = dec16(*pq) + wt<float>(q) * (t.x + sgn * ev) + extra;
       }
     } else {
       pull_face_ref(a.src, r.ref_src, a.qstride, a.nx, a.ny, a.nz, a.pitch, a.plane, a.facebits,
@@ -385,10 +391,12 @@ __device__ void ref_stage_batch(const LatDesc<float>& L, int parity, int x0, int
   const uint2* rs = static_cast<const uint2*>(L.ref[parity]);
   const int sx = tw + 2, sxy = sx * (th + 2);
   const int lx = lin & (tw - 1), ly = lin >> twl;
+  const bool xper = (L.facebits & 3u) == unsigned(BC_PERIODIC);
   for (int ky = ly; ky < th + 2; ky += th) {
     const int gy = y0 - 1 + ky;
     for (int kx = lx; kx < sx; kx += tw) {
-      const int gx = x0 - 1 + kx;
+      int gx = x0 - 1 + kx;
+      if (xper) gx = gx == -1 ? L.nx - 1 : gx == L.nx ? 0 : gx;
       const bool in = gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny;
       const int gi = (z - 1) * L.plane + gy * L.pitch + gx;
 #pragma unroll
@@ -417,28 +425,27 @@ __device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y
   const int i = z * plane + y * pitch + x;
   float d[Q];
   if (y > 0 && y < L.ny - 1 && z > 0 && z < L.nz - 1) {
+    // as in step_ref_kernel: one load per direction, x faces by a select
+    const bool fl = x == 0, fr = x == L.nx - 1;
+    const int kl = L.facebits & 3, kr = (L.facebits >> 2) & 3;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const int j = i - (cz(q) * plane + cy(q) * pitch + cx(q));
-      const float4 t = sref[-cz(q) * sxy - cy(q) * sx - cx(q)];
-      d[q] = dec16(src[q * qs + j]) + ref_term(q, Ref4{t.x, t.y, t.z, t.w}, rho0);
-    }
-    if (x == 0 || x == L.nx - 1) {
-      const int kl = L.facebits & 3, kr = (L.facebits >> 2) & 3;
-#pragma unroll
-      for (int q = 1; q < Q; ++q) {
-        const bool left = cx(q) == 1 && x == 0, right = cx(q) == -1 && x == L.nx - 1;
-        if (left || right) {
-          const int k = left ? kl : kr;
-          if (k == BC_PERIODIC) {
-            const int j = i - (cz(q) * plane + cy(q) * pitch + cx(q)) + (left ? L.nx : -L.nx);
-            d[q] = dec16(src[q * qs + j]) + ref_term(q, ref_load(rs + j), rho0);
-          } else {
-            d[q] = dec16(src[opp(q) * qs + i]) + ref_term(opp(q), ref_load(rs + i), rho0) +
-                   (k == BC_LID ? L.lidc[q] : 0.0f);
-          }
+      int j = q * qs + i - (cz(q) * plane + cy(q) * pitch + cx(q));
+      float4 t = sref[-cz(q) * sxy - cy(q) * sx - cx(q)];
+      float sgn = 1.0f, extra = 0.0f;
+      if ((cx(q) == 1 && fl) || (cx(q) == -1 && fr)) {
+        const int k = cx(q) == 1 ? kl : kr;
+        if (k == BC_PERIODIC) {
+          j += cx(q) == 1 ? L.nx : -L.nx;
+        } else {
+          j = opp(q) * qs + i;
+          t = sref[0];
+          sgn = -1.0f;
+          extra = k == BC_LID ? L.lidc[q] : 0.0f;
         }
       }
+      const float ev = float(cx(q)) * t.y + float(cy(q)) * t.z + float(cz(q)) * t.w;
+      d[q] = dec16(src[j]) + wt<float>(q) * (t.x + sgn * ev) + extra;
     }
   } else {
     pull_face_ref(src, rs, L.qstride, L.nx, L.ny, L.nz, pitch, plane, L.facebits, x, y, z, i,
