@@ -69,7 +69,7 @@ __device__ __forceinline__ void batch_node(const LatDesc<R>& L, const S* __restr
     pull_face<S, R>(src, L.qstride, L.nx, L.ny, L.nz, pitch, plane, L.facebits, x, y, z, i,
                     L.lidc, d);
   }
-  collide<R, FORCE, pair_out<S>()>(L.C, d, o);
+  collide<R, FORCE, pair_out<S>(), log2_scale<S>()>(L.C, d, o);
 #pragma unroll
   for (int q = 0; q < Q; ++q) dst[q * qs + i] = Codec<S, R>::enc(d[q], R(1));
 }
@@ -238,7 +238,8 @@ constexpr int BATCH_CONST_BYTES = 60 * 1024;
 
 // Host-side fill of one descriptor (constants converted once, in double).
 template <typename R>
-void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur, const void* other,
+void fill_desc_t(void* out, double lam, const Geom& g, const PhysParams& P, const void* cur,
+                 const void* other,
                  const void* ref_cur, const void* ref_other, void* uprev, int tiles_x,
                  int tiles_y, int tw_log2, int slot, unsigned step_offset) {
   LatDesc<R> L{};
@@ -260,9 +261,9 @@ void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur,
   L.slot = slot;
   L.step_offset = step_offset;
   for (int q = 0; q < Q; ++q)
-    L.lidc[q] = R(6.0 * wt<double>(q) * g.rho0 *
+    L.lidc[q] = R(6.0 * wt<double>(q) * g.rho0 * lam *
                   (cx(q) * g.U[0] + cy(q) * g.U[1] + cz(q) * g.U[2]));
-  L.C = make_const<R>(P);
+  L.C = make_const<R>(P, lam);
   *static_cast<LatDesc<R>*>(out) = L;
 }
 
@@ -314,7 +315,9 @@ void fill_desc_t(void* out, const Geom& g, const PhysParams& P, const void* cur,
   void fill_desc_##SUFFIX(void* out, const Geom& g, const PhysParams& P, const void* cur,        \
                           const void* other, const void* ref_cur, const void* ref_other,       \
                           void* uprev, int tx, int ty, int twl, int slot, unsigned so) {       \
-    fill_desc_t<R>(out, g, P, cur, other, ref_cur, ref_other, uprev, tx, ty, twl, slot, so);   \
+    /* the F16R form carries unscaled deviations; FP16-shifted ones are scaled */            \
+    fill_desc_t<R>(out, REF ? 1.0 : double(1 << log2_scale<S>()), g, P, cur, other, ref_cur,   \
+                   ref_other, uprev, tx, ty, twl, slot, so);                                   \
   }                                                                                            \
   cudaError_t upload_desc_##SUFFIX(const void* host, int base, int n) {                        \
     return cudaMemcpyToSymbol(c_lat_##SUFFIX, host, size_t(n) * sizeof(LatDesc<R>),            \

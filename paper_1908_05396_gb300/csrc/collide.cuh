@@ -25,6 +25,8 @@ template <typename R>
 struct CollideConst {
   R rho0;
   R F[3];        // body force
+  R rhoS;        // lam rho0 and lam F: rest density and force of deviations
+  R FS[3];       //   carried scaled by lam (FP16 storage: lam = 1024; else 1)
   R K3;          // 3 K (K = mu_p, consistency coefficient, Eq. 5)
   R logK3;       // log(3 K)
   R log2K3;      // log2(3 K)
@@ -499,7 +501,16 @@ __device__ __forceinline__ void strain_AB(const CollideConst<T>& C, R rinv, R m4
 // (sums of a few of them need no rounding), or as one correction added to
 // each input population (add_K_g), which keeps FP32 populations to a single
 // rounding per step.
-template <typename R, bool FORCE, bool PAIR_OUT = false>
+//
+// LOG2LAM: the deviations are carried scaled by lam = 2^LOG2LAM (the FP16
+// storage scale), and C holds lam rho0, lam F, lam 3K and log(lam 3K).  All
+// moments and g^ then scale with lam, rho becomes lam rho and 1/rho
+// 1/(lam rho): every term is either linear in the deviations or a product
+// whose factors of lam cancel (the attractors a_i a_j / rho, the strain rate
+// of m^(1)/rho, the omega solve of 3K/rho), so the scaled populations come
+// out exactly as lam times the unscaled ones up to rounding, and only rho
+// is unscaled for the output.
+template <typename R, bool FORCE, bool PAIR_OUT = false, int LOG2LAM = 0>
 __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>::type>& C,
                                         R (&d)[Q], NodeOut<R>& out) {
   using T = typename ScalarOf<R>::type;
@@ -512,16 +523,16 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
   const R drho = p.d0 + (p.sAx + p.sAy + p.sAz) + (p.Dxxyy + p.Dxxzz + p.Dyyzz);
   const R jx = p.tAx + (p.Dxyy + p.Dxzz), jy = p.tAy + (p.Dxxy + p.Dyzz),
           jz = p.tAz + (p.Dxxz + p.Dyyz);
-  const R rho = R(C.rho0) + drho;
+  const R rho = R(C.rhoS) + drho;
   const R rinv = rrcp<R>(rho);
   R ux, uy, uz;
   if (FORCE) {
     // Symmetric split of the body force: the velocity is (j + F/2)/rho and
     // half of the source is added before the collision, half after.
-    ux = (jx + R(T(0.5) * C.F[0])) * rinv;
-    uy = (jy + R(T(0.5) * C.F[1])) * rinv;
-    uz = (jz + R(T(0.5) * C.F[2])) * rinv;
-    add_half_source(p, ux, uy, uz, C.F);
+    ux = (jx + R(T(0.5) * C.FS[0])) * rinv;
+    uy = (jy + R(T(0.5) * C.FS[1])) * rinv;
+    uz = (jz + R(T(0.5) * C.FS[2])) * rinv;
+    add_half_source(p, ux, uy, uz, C.FS);
   } else {
     ux = jx * rinv;
     uy = jy * rinv;
@@ -538,7 +549,7 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
           Dzz = p.sAz + (Dxxzz + Dyyzz);
 
   const R ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz;
-  const R r3 = R(C.rho0 * T(1.0 / 3.0));
+  const R r3 = R(C.rhoS * T(1.0 / 3.0));
   const R kxx = r3 + Dxx, kyy = r3 + Dyy, kzz = r3 + Dzz;
 
   // ---- non-equilibrium second moments m^(1)_4..9 (Sec. 3.2) -------------
@@ -634,12 +645,13 @@ __device__ __forceinline__ void collide(const CollideConst<typename ScalarOf<R>:
 
   // ---- back-transform f~ = f + K g^ (+ second half of the source) --------
   if constexpr (PAIR_OUT) {
-    if (FORCE) add_half_source(p, ux, uy, uz, C.F);
+    if (FORCE) add_half_source(p, ux, uy, uz, C.FS);
     from_pairs(p, g, d);
   } else {
-    add_K_g<R, FORCE>(d, g, ux, uy, uz, C.F);
+    add_K_g<R, FORCE>(d, g, ux, uy, uz, C.FS);
   }
-  out.rho = rho;
+  if constexpr (LOG2LAM != 0) out.rho = rho * R(T(1.0 / double(1 << LOG2LAM)));
+  else out.rho = rho;
   out.ux = ux;
   out.uy = uy;
   out.uz = uz;

@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_aa_kernel(const StepArg
                        a.lidc, d);
     }
     NodeOut<R> o;
-    collide<R, FORCE, pair_out<S>()>(a.C, d, o);
+    collide<R, FORCE, pair_out<S>(), log2_scale<S>()>(a.C, d, o);
     if (LIN == 1) {
 #pragma unroll
       for (int q = 0; q < Q; ++q) a.dstq[q][i] = Codec<S, R>::enc(d[q], R(1));
@@ -212,17 +212,18 @@ __global__ void __launch_bounds__(256) fields_aa_kernel(const S* __restrict__ A,
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= g.nx || y >= g.ny) return;
-  const CollideConst<R> C = make_const<R>(P);
+  const CollideConst<R> C = make_const<R>(P, double(1 << log2_scale<S>()));
   R lidc[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q)
-    lidc[q] = R(6.0 * wt<double>(q) * g.rho0 * (cx(q) * g.U[0] + cy(q) * g.U[1] + cz(q) * g.U[2]));
+    lidc[q] = R(6.0 * wt<double>(q) * g.rho0 * double(1 << log2_scale<S>()) *
+                (cx(q) * g.U[0] + cy(q) * g.U[1] + cz(q) * g.U[2]));
   const int i = z * int(g.plane) + y * g.pitch + x;
   R d[Q];
   aa_read<S, R, L>(A, g.qstride, x, y, z, i, g.nx, g.ny, g.nz, g.pitch, int(g.plane), g.facebits,
                    lidc, d);
   NodeOut<R> o;
-  collide<R, FORCE, pair_out<S>()>(C, d, o);
+  collide<R, FORCE, pair_out<S>(), log2_scale<S>()>(C, d, o);
   const int64_t N = int64_t(g.nx) * g.ny * g.nz;
   const int64_t k = (int64_t(z) * g.ny + y) * g.nx + x;
   if (rho) rho[k] = double(o.rho);
@@ -263,7 +264,7 @@ __global__ void export_aa_kernel(const S* __restrict__ A, Geom g, double rho0, d
       j = int64_t(q) * g.qstride + int64_t(zd) * g.plane + int64_t(yd) * g.pitch + xd;
     }
   }
-  out[t] = double(Codec<S, double>::dec(A[j], inv_scale)) + wt<double>(q) * rho0;
+  out[t] = double(Codec<S, double>::dec(A[j], inv_scale)) * inv_scale + wt<double>(q) * rho0;
 }
 
 // Import a state f~ into layout 0.
@@ -278,7 +279,7 @@ __global__ void import_aa_kernel(const double* __restrict__ in, Geom g, double r
   const int x = int(k % g.nx), y = int((k / g.nx) % g.ny), z = int(k / (int64_t(g.nx) * g.ny));
   const int64_t i = int64_t(z) * g.plane + int64_t(y) * g.pitch + x;
   A[int64_t(c_opp[q]) * g.qstride + i] =
-      Codec<S, double>::enc(in[t] - wt<double>(q) * rho0, inv_scale);
+      Codec<S, double>::enc((in[t] - wt<double>(q) * rho0) / inv_scale, inv_scale);
 }
 
 // ---- host-side launchers ------------------------------------------------------
@@ -297,7 +298,7 @@ cudaError_t launch_step_aa_t(void* buf, const Geom& g, const PhysParams& P, cons
     const int64_t dq = layout == 0 ? int64_t(q) * g.qstride + off : int64_t(opp(q)) * g.qstride;
     a.srcq[q] = reinterpret_cast<const S*>(base + sq * int64_t(sizeof(S)));
     a.dstq[q] = reinterpret_cast<S*>(base + dq * int64_t(sizeof(S)));
-    a.lidc[q] = R(6.0 * wt<double>(q) * g.rho0 *
+    a.lidc[q] = R(6.0 * wt<double>(q) * g.rho0 * double(1 << log2_scale<S>()) *
                   (cx(q) * g.U[0] + cy(q) * g.U[1] + cz(q) * g.U[2]));
   }
   a.src = A;
@@ -308,7 +309,7 @@ cudaError_t launch_step_aa_t(void* buf, const Geom& g, const PhysParams& P, cons
   a.pitch = g.pitch;
   a.plane = int(g.plane);
   a.facebits = g.facebits;
-  a.C = make_const<R>(P);
+  a.C = make_const<R>(P, double(1 << log2_scale<S>()));
   a.cb = cb;
   const bool cap = (npt & 4) != 0;
   const dim3 grid((g.nx + block.x - 1) / block.x, (g.ny + block.y - 1) / block.y, g.nz);

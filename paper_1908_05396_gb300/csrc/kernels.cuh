@@ -33,14 +33,20 @@ template <typename R> struct Codec<float, R> {
 template <typename R> struct Codec<__half, R> {
   // (f - w rho0) * 1024 in FP16, round to nearest even.  The power-of-two
   // scale is exact and lifts deviations down to ~6e-8 out of the FP16
-  // subnormal range while keeping |f - w rho0| < 64 representable.
-  static __device__ __forceinline__ R dec(__half v, R) {
-    return R(__half2float(v)) * R(1.0 / F16_SCALE);
-  }
-  static __device__ __forceinline__ __half enc(R v, R) {
-    return __float2half_rn(float(v) * float(F16_SCALE));
-  }
+  // subnormal range while keeping |f - w rho0| < 64 representable.  The
+  // kernels work on the scaled deviations directly (log2_scale): the scale
+  // is folded into the collision's constants, so decoding and encoding are
+  // plain conversions.
+  static __device__ __forceinline__ R dec(__half v, R) { return R(__half2float(v)); }
+  static __device__ __forceinline__ __half enc(R v, R) { return __float2half_rn(float(v)); }
 };
+
+// log2 of the factor by which storage type S holds the deviations f - w rho0
+// (and by which the kernels carry them): 10 for FP16, 0 otherwise.
+template <typename S>
+__host__ __device__ constexpr int log2_scale() {
+  return std::is_same<S, __half>::value ? 10 : 0;
+}
 
 // Whether the collision rebuilds the populations of storage type S from its
 // pair values (see collide): for FP16 storage, whose decoded values sum
@@ -51,16 +57,24 @@ __host__ __device__ constexpr bool pair_out() {
   return std::is_same<S, __half>::value || std::is_same<S, double>::value;
 }
 
+// Collision constants for deviations carried scaled by lam (a power of two;
+// see collide): the rest density and the force of the scaled moments, and
+// 3K, log(3K) so that nu and the omega solve come out unscaled.
 template <typename R>
-__host__ __device__ __forceinline__ CollideConst<R> make_const(const PhysParams& P) {
+__host__ __device__ __forceinline__ CollideConst<R> make_const(const PhysParams& P,
+                                                             double lam = 1.0) {
   CollideConst<R> C;
   C.rho0 = R(P.rho0);
+  C.rhoS = R(lam * P.rho0);
+  C.FS[0] = R(lam * P.F[0]);
+  C.FS[1] = R(lam * P.F[1]);
+  C.FS[2] = R(lam * P.F[2]);
   C.F[0] = R(P.F[0]);
   C.F[1] = R(P.F[1]);
   C.F[2] = R(P.F[2]);
-  C.K3 = R(3.0 * P.K);
-  C.logK3 = R(P.logK3);
-  C.log2K3 = R(P.logK3 * 1.4426950408889634074);
+  C.K3 = R(3.0 * P.K * lam);
+  C.logK3 = R(P.logK3 + log(lam));
+  C.log2K3 = R(P.logK3 * 1.4426950408889634074 + log2(lam));
   C.n = R(P.n);
   C.rn = R(1.0 / P.n);
   C.ehalf = R(0.5 * (P.n - 1.0));
@@ -90,7 +104,7 @@ __host__ __device__ __forceinline__ CollideConst<R> make_const(const PhysParams&
 // Pull the 19 pre-collision deviations of node (x, y, z).
 template <typename S, typename R>
 __device__ __forceinline__ void pull(const S* __restrict__ src, const Geom& g,
-                                     int x, int y, int z, int64_t i, R inv_scale,
+                                     int x, int y, int z, int64_t i, R lam,
                                      R (&d)[Q]) {
   const bool interior = x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 &&
                         z > 0 && z < g.nz - 1;
@@ -98,7 +112,7 @@ __device__ __forceinline__ void pull(const S* __restrict__ src, const Geom& g,
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int64_t off = int64_t(cz(q)) * g.plane + int64_t(cy(q)) * g.pitch + cx(q);
-      d[q] = Codec<S, R>::dec(src[q * g.qstride + i - off], inv_scale);
+      d[q] = Codec<S, R>::dec(src[q * g.qstride + i - off], lam);
     }
     return;
   }
@@ -122,14 +136,14 @@ __device__ __forceinline__ void pull(const S* __restrict__ src, const Geom& g,
     if (bounce) {
       // Halfway bounce-back f_q(x) = f~_opp(q)(x); a lid adds
       // 6 w_q rho0 (e_q . U), which is the same for deviations.
-      R v = Codec<S, R>::dec(src[opp(q) * g.qstride + i], inv_scale);
+      R v = Codec<S, R>::dec(src[opp(q) * g.qstride + i], lam);
       if (lid)
-        v += R(6) * wt<R>(q) * R(g.rho0) *
+        v += lam * R(6) * wt<R>(q) * R(g.rho0) *
              (R(cx(q)) * R(g.U[0]) + R(cy(q)) * R(g.U[1]) + R(cz(q)) * R(g.U[2]));
       d[q] = v;
     } else {
       const int64_t j = int64_t(s[2]) * g.plane + int64_t(s[1]) * g.pitch + s[0];
-      d[q] = Codec<S, R>::dec(src[q * g.qstride + j], inv_scale);
+      d[q] = Codec<S, R>::dec(src[q * g.qstride + j], lam);
     }
   }
 }
@@ -314,7 +328,7 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_kernel(const StepArgs<S
                       i, a.lidc, d);
     }
     NodeOut<R> o;
-    collide<R, FORCE, pair_out<S>()>(a.C, d, o);
+    collide<R, FORCE, pair_out<S>(), log2_scale<S>()>(a.C, d, o);
 #pragma unroll
     for (int q = 0; q < Q; ++q) a.dstq[q][i] = Codec<S, R>::enc(d[q], R(1));
     if (CHECK) {
@@ -401,7 +415,7 @@ __global__ void __launch_bounds__(128, CAP ? 4 : 1) step2_kernel(const StepArgs<
       for (int q = 0; q < Q; ++q) d[q] = V2(dA[q], dB[q]);
     }
     NodeOut<V2> o;
-    collide<V2, FORCE, pair_out<S>()>(a.C, d, o);
+    collide<V2, FORCE, pair_out<S>(), log2_scale<S>()>(a.C, d, o);
 #pragma unroll
     for (int q = 0; q < Q; ++q) a.dstq[q][iA] = Codec<S, float>::enc(lane0(d[q]), 1.0f);
     if (activeB) {
@@ -451,13 +465,13 @@ __global__ void __launch_bounds__(256) fields_kernel(const S* __restrict__ src, 
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= g.nx || y >= g.ny) return;
-  const R inv_scale = R(P.inv_scale);
-  const CollideConst<R> C = make_const<R>(P);
+  const double lam = double(1 << log2_scale<S>());
+  const CollideConst<R> C = make_const<R>(P, lam);
   const int64_t i = int64_t(z) * g.plane + int64_t(y) * g.pitch + x;
   R d[Q];
-  pull<S, R>(src, g, x, y, z, i, inv_scale, d);
+  pull<S, R>(src, g, x, y, z, i, R(lam), d);
   NodeOut<R> o;
-  collide<R, FORCE, pair_out<S>()>(C, d, o);
+  collide<R, FORCE, pair_out<S>(), log2_scale<S>()>(C, d, o);
   const int64_t N = int64_t(g.nx) * g.ny * g.nz;
   const int64_t k = (int64_t(z) * g.ny + y) * g.nx + x;
   if (rho) rho[k] = double(o.rho);
@@ -476,20 +490,20 @@ __global__ void collide_nodes_kernel(PhysParams P, const double* __restrict__ fi
                                      double* u, double* gd, int64_t M) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= M) return;
-  const R inv_scale = R(P.inv_scale);
-  const CollideConst<R> C = make_const<R>(P);
+  const double lam = double(1 << log2_scale<S>());
+  const CollideConst<R> C = make_const<R>(P, lam);
   R d[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    const R dev = R(fin[q * M + k] - wt<double>(q) * P.rho0);
-    d[q] = Codec<S, R>::dec(Codec<S, R>::enc(dev, inv_scale), inv_scale);
+    const R dev = R((fin[q * M + k] - wt<double>(q) * P.rho0) * lam);
+    d[q] = Codec<S, R>::dec(Codec<S, R>::enc(dev, R(lam)), R(lam));
   }
   NodeOut<R> o;
-  collide<R, FORCE, pair_out<S>()>(C, d, o);
+  collide<R, FORCE, pair_out<S>(), log2_scale<S>()>(C, d, o);
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    const R st = Codec<S, R>::dec(Codec<S, R>::enc(d[q], inv_scale), inv_scale);
-    fout[q * M + k] = double(st) + wt<double>(q) * P.rho0;
+    const R st = Codec<S, R>::dec(Codec<S, R>::enc(d[q], R(lam)), R(lam));
+    fout[q * M + k] = double(st) / lam + wt<double>(q) * P.rho0;
   }
   if (rho) rho[k] = double(o.rho);
   if (u) {
@@ -533,7 +547,7 @@ __global__ void export_kernel(const S* __restrict__ src, Geom g, double rho0,
   const int x = int(k % g.nx), y = int((k / g.nx) % g.ny), z = int(k / (int64_t(g.nx) * g.ny));
   const int64_t i = int64_t(z) * g.plane + int64_t(y) * g.pitch + x;
   const double w = wt<double>(q);
-  out[t] = double(Codec<S, double>::dec(src[q * g.qstride + i], inv_scale)) + w * rho0;
+  out[t] = double(Codec<S, double>::dec(src[q * g.qstride + i], inv_scale)) * inv_scale + w * rho0;
 }
 
 template <typename S>
@@ -547,7 +561,7 @@ __global__ void import_kernel(const double* __restrict__ in, Geom g, double rho0
   const int x = int(k % g.nx), y = int((k / g.nx) % g.ny), z = int(k / (int64_t(g.nx) * g.ny));
   const int64_t i = int64_t(z) * g.plane + int64_t(y) * g.pitch + x;
   const double w = wt<double>(q);
-  dst[q * g.qstride + i] = Codec<S, double>::enc(in[t] - w * rho0, inv_scale);
+  dst[q * g.qstride + i] = Codec<S, double>::enc((in[t] - w * rho0) / inv_scale, inv_scale);
 }
 
 }  // namespace clbm
@@ -572,7 +586,7 @@ cudaError_t launch_step_t(const void* src, void* dst, const Geom& g, const PhysP
     a.srcq[q] = reinterpret_cast<const S*>(reinterpret_cast<uintptr_t>(s) +
                                             (int64_t(q) * g.qstride - off) * int64_t(sizeof(S)));
     a.dstq[q] = d + int64_t(q) * g.qstride;
-    a.lidc[q] = R(6.0 * wt<double>(q) * g.rho0 *
+    a.lidc[q] = R(6.0 * wt<double>(q) * g.rho0 * double(1 << log2_scale<S>()) *
                   (cx(q) * g.U[0] + cy(q) * g.U[1] + cz(q) * g.U[2]));
   }
   a.src = s;
@@ -588,7 +602,7 @@ cudaError_t launch_step_t(const void* src, void* dst, const Geom& g, const PhysP
   // (the steps that write the lower-addressed of the two buffers) makes the
   // next step read those planes first, from L2.
   a.zrev = reinterpret_cast<uintptr_t>(dst) < reinterpret_cast<uintptr_t>(src) ? 1 : 0;
-  a.C = make_const<R>(P);
+  a.C = make_const<R>(P, double(1 << log2_scale<S>()));
   a.cb = cb;
   // npt: 1 or 2 nodes per thread; +4 selects the register-capped variant;
   // TMA_NPT + 32 v the TMA-staged kernel of shape v (check steps take the

@@ -59,17 +59,17 @@ __global__ void __launch_bounds__(256) step_partials_kernel(const S* __restrict_
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   const bool active = x < g.nx && y < g.ny;
-  const R inv_scale = R(P.inv_scale);
-  const CollideConst<R> C = make_const<R>(P);
+  const double lam = double(1 << log2_scale<S>());
+  const CollideConst<R> C = make_const<R>(P, lam);
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   if (active) {
     const int64_t i = int64_t(z) * g.plane + int64_t(y) * g.pitch + x;
     R d[Q];
-    pull<S, R>(src, g, x, y, z, i, inv_scale, d);
+    pull<S, R>(src, g, x, y, z, i, R(lam), d);
     NodeOut<R> o;
-    collide<R, FORCE, pair_out<S>()>(C, d, o);
+    collide<R, FORCE, pair_out<S>(), log2_scale<S>()>(C, d, o);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) dst[q * g.qstride + i] = Codec<S, R>::enc(d[q], inv_scale);
+    for (int q = 0; q < Q; ++q) dst[q * g.qstride + i] = Codec<S, R>::enc(d[q], R(lam));
     const int64_t nst = g.plane * g.nz;
     const R px = uprev[i], py = uprev[nst + i], pz = uprev[2 * nst + i];
     uprev[i] = o.ux;

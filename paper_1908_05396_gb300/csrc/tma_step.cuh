@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(BX * BY / NP, MINB)
       face_fix(a, x, y, z, i, d);
       if constexpr (NP == 1) {
         NodeOut<float> o;
-        collide<float, FORCE, pair_out<S>()>(a.C, d, o);
+        collide<float, FORCE, pair_out<S>(), log2_scale<S>()>(a.C, d, o);
 #pragma unroll
         for (int q = 0; q < Q; ++q) a.dstq[q][i] = Codec<S, float>::enc(d[q], 1.0f);
       } else {
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(BX * BY / NP, MINB)
 #pragma unroll
         for (int q = 0; q < Q; ++q) p[q] = V2(d[q], dB[q]);
         NodeOut<V2> o;
-        collide<V2, FORCE, pair_out<S>()>(a.C, p, o);
+        collide<V2, FORCE, pair_out<S>(), log2_scale<S>()>(a.C, p, o);
 #pragma unroll
         for (int q = 0; q < Q; ++q) a.dstq[q][i] = Codec<S, float>::enc(lane0(p[q]), 1.0f);
         if (activeB) {
