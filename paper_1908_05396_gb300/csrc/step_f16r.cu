@@ -74,15 +74,20 @@ __device__ __forceinline__ uint32_t sr_seed(uint32_t node, uint32_t step) {
 
 // Two values at once with the GB300's stochastic-rounding conversion
 // (cvt.rs.f16x2.f32: each value rounded up in magnitude with the probability
-// of the fraction of an FP16 ulp it carries, using the random bits given).
-// One 32-bit step of the generator above feeds both; hi receives a, lo b.
+// of the fraction of an FP16 ulp it carries).  hi receives a, lo b; the
+// conversion adds the low 13 bits of each 16-bit half of the random word
+// below the kept mantissa (measured: bits 0-12 round b, bits 16-28 round a).
+// One 32-bit step of the generator above feeds both, with its upper half
+// folded into the lower one: the low bits of a power-of-two-modulus LCG
+// have short periods, its high bits do not.
 __device__ __forceinline__ void enc16_sr2(float a, float b, uint32_t& state, __half& hi,
                                           __half& lo) {
   state = state * 747796405u + 2891336453u;
+  const uint32_t rbits = state ^ (state >> 16);
   uint32_t d;
   asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;"
       : "=r"(d)
-      : "f"(a * float(F16_SCALE)), "f"(b * float(F16_SCALE)), "r"(state));
+      : "f"(a * float(F16_SCALE)), "f"(b * float(F16_SCALE)), "r"(rbits));
   hi = __ushort_as_half(static_cast<unsigned short>(d >> 16));
   lo = __ushort_as_half(static_cast<unsigned short>(d & 0xFFFFu));
 }
