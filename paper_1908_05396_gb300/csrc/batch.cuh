@@ -76,33 +76,9 @@ __device__ __forceinline__ void batch_node(const LatDesc<R>& L, const S* __restr
 
 // One node of the batched step in the F16R form (defined with the other F16R
 // kernels, the only translation unit that instantiates the batch with REF).
-// `sref`, when not null, points at the node's own entry of the block's
-// staged reference moments (ref_stage_batch), `sx` and `sxy` being the row
-// and plane strides of the staged box; interior nodes then read their
-// upwind neighbours' references from there.
 template <bool FORCE>
 __device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y, int z,
-                               unsigned step, NodeOut<float>& o, const float4* sref, int sx,
-                               int sxy);
-
-// Stage the reference moments of a tile's nodes and their neighbours (the
-// tile's x range widened by one node on each side, the same for y, planes
-// z - 1 .. z + 1) into shared memory, decoded to FP32, for the F16R batch.
-// Nodes outside the lattice are staged as zeros (never read: their readers
-// are face nodes).  Called by every thread of the block.
-__device__ void ref_stage_batch(const LatDesc<float>& L, int parity, int x0, int y0, int z,
-                                int tw, int th, int lin, int twl, float4* sref);
-
-// Largest staged box of a block of `threads` threads over the tile widths a
-// lattice can choose (powers of two from 8 up to the block's x extent).
-__host__ __device__ inline size_t ref_stage_batch_bytes(int bx, int threads) {
-  size_t best = 0;
-  for (int tw = 8; tw <= bx; tw *= 2) {
-    const size_t b = size_t(3) * size_t(tw + 2) * size_t(threads / tw + 2) * 16;
-    if (b > best) best = b;
-  }
-  return best;
-}
+                               unsigned step, NodeOut<float>& o);
 
 // tile word: x tile (8 bits) | y tile (12 bits) | z chunk (12 bits)
 __host__ __device__ __forceinline__ unsigned tile_word(int tx, int ty, int tz) {
@@ -166,27 +142,9 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
     const int z1 = min(tz * zc + zc, L.nz);
 #pragma unroll 1
     for (int z = tz * zc; z < z1; ++z) {
-      const float4* sr = nullptr;
-      int sx = 0, sxy = 0;
-      if constexpr (REF) {
-        // F16R: the tile's references, staged once per plane (block-uniform
-        // condition: the whole tile lies in one plane)
-        if (z > 0 && z < L.nz - 1) {
-          extern __shared__ float4 sref_b[];
-          const int tw = 1 << L.tw_log2, th = int(blockDim.x * blockDim.y) >> L.tw_log2;
-          __syncthreads();  // the previous plane's box has been read
-          ref_stage_batch(L, parity, tx << L.tw_log2, ty * th, z, tw, th, lin, L.tw_log2,
-                          sref_b);
-          __syncthreads();
-          sx = tw + 2;
-          sxy = sx * (th + 2);
-          sr = sref_b + sxy + ((lin >> L.tw_log2) + 1) * sx + (lin & (tw - 1)) + 1;
-        }
-      }
       if (active) {
         NodeOut<R> o;
-        if constexpr (REF)
-          batch_node_ref<FORCE>(L, parity, x, y, z, bstep + L.step_offset, o, sr, sx, sxy);
+        if constexpr (REF) batch_node_ref<FORCE>(L, parity, x, y, z, bstep + L.step_offset, o);
         else batch_node<S, R, FORCE>(L, src, dst, x, y, z, o);
         if (CHECK) {
           R* up = static_cast<R*>(L.uprev);
@@ -286,26 +244,24 @@ void fill_desc_t(void* out, double lam, const Geom& g, const PhysParams& P, cons
                                     int zc, dim3 block, int grid, cudaStream_t st,             \
                                     cudaStream_t stf) {                                         \
     BatchHeader* H = static_cast<BatchHeader*>(const_cast<void*>(hdr));                        \
-    const size_t smem_ =                                                                       \
-        REF ? ref_stage_batch_bytes(int(block.x), int(block.x * block.y)) : size_t(0);         \
     const bool cap = grid < 0;                                                                 \
     if (cap) grid = -grid;                                                                     \
     /* tiles without force on st, tiles with force on stf (an empty range exits at once) */   \
     if (check) {                                                                               \
       if (cap) {                                                                               \
-        batch_kernel_##SUFFIX<true, true, false><<<grid, block, smem_, st>>>(base, owner, coord, H, parity, acc, zc); \
-        batch_kernel_##SUFFIX<true, true, true><<<grid, block, smem_, stf>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<true, true, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<true, true, true><<<grid, block, 0, stf>>>(base, owner, coord, H, parity, acc, zc); \
       } else {                                                                                 \
-        batch_kernel_##SUFFIX<true, false, false><<<grid, block, smem_, st>>>(base, owner, coord, H, parity, acc, zc); \
-        batch_kernel_##SUFFIX<true, false, true><<<grid, block, smem_, stf>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<true, false, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<true, false, true><<<grid, block, 0, stf>>>(base, owner, coord, H, parity, acc, zc); \
       }                                                                                        \
     } else {                                                                                   \
       if (cap) {                                                                               \
-        batch_kernel_##SUFFIX<false, true, false><<<grid, block, smem_, st>>>(base, owner, coord, H, parity, acc, zc); \
-        batch_kernel_##SUFFIX<false, true, true><<<grid, block, smem_, stf>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<false, true, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<false, true, true><<<grid, block, 0, stf>>>(base, owner, coord, H, parity, acc, zc); \
       } else {                                                                                 \
-        batch_kernel_##SUFFIX<false, false, false><<<grid, block, smem_, st>>>(base, owner, coord, H, parity, acc, zc); \
-        batch_kernel_##SUFFIX<false, false, true><<<grid, block, smem_, stf>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<false, false, false><<<grid, block, 0, st>>>(base, owner, coord, H, parity, acc, zc); \
+        batch_kernel_##SUFFIX<false, false, true><<<grid, block, 0, stf>>>(base, owner, coord, H, parity, acc, zc); \
       }                                                                                        \
     }                                                                                          \
     return cudaGetLastError();                                                                 \

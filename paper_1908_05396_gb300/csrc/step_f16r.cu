@@ -155,54 +155,14 @@ __device__ __forceinline__ void pull_face_ref(const __half* __restrict__ src,
   }
 }
 
-// Shared memory of one block of the step: the reference moments of its
-// nodes and their neighbours, (bx + 2) x (by + 2) nodes in each of the
-// planes z - 1, z, z + 1, decoded to FP32 once per block.
-__host__ __device__ inline size_t ref_stage_bytes(int bx, int by) {
-  return size_t(3) * size_t(bx + 2) * size_t(by + 2) * sizeof(float4);
-}
-
 template <bool FORCE, bool CHECK, bool CAP>
 __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepArgs<__half, float> a,
                                                                     const RefArgs r) {
-  extern __shared__ float4 sref[];
   pdl_enter();
-  const int bx = int(blockDim.x), by = int(blockDim.y);
-  const int sx = bx + 2, sxy = sx * (by + 2);
-  const int x = blockIdx.x * bx + threadIdx.x;
-  const int y = blockIdx.y * by + threadIdx.y;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = a.zrev ? a.nz - 1 - int(blockIdx.z) : int(blockIdx.z);  // as step_kernel
   const bool active = x < a.nx && y < a.ny;
-  // Blocks off the z faces stage the references that their interior nodes
-  // read (every upwind neighbour lies in the staged box, the periodic wrap
-  // along x included), instead of one 8-byte load and conversion per
-  // direction and node.  Nodes outside the lattice are staged as zeros and
-  // never read: their readers are y or z face nodes, which take
-  // pull_face_ref, or x face nodes, which bounce back.
-  const bool zin = z > 0 && z < a.nz - 1;  // block-uniform
-  if (zin) {
-    const int x0 = int(blockIdx.x) * bx - 1, y0 = int(blockIdx.y) * by - 1;
-    const bool xper = (a.facebits & 3u) == unsigned(BC_PERIODIC);
-    for (int ky = threadIdx.y; ky < by + 2; ky += by) {
-      const int gy = y0 + ky;
-      for (int kx = threadIdx.x; kx < sx; kx += bx) {
-        int gx = x0 + kx;
-        if (xper) gx = gx == -1 ? a.nx - 1 : gx == a.nx ? 0 : gx;
-        const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny;
-        const int gi = (z - 1) * a.plane + gy * a.pitch + gx;
-#pragma unroll
-        for (int kz = 0; kz < 3; ++kz) {
-          float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-          if (in) {
-            const Ref4 t = ref_load(r.ref_src + gi + kz * a.plane);
-            v = make_float4(t.dr, t.vx, t.vy, t.vz);
-          }
-          sref[kz * sxy + ky * sx + kx] = v;
-        }
-      }
-    }
-    __syncthreads();
-  }
   if (!CHECK && !active) return;
   const float rho0 = a.C.rho0;
   double du2 = 0.0, uu = 0.0, dr = 0.0;
@@ -210,33 +170,35 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
   if (active) {
     const int i = z * a.plane + y * a.pitch + x;
     float d[Q];
-    if (y > 0 && y < a.ny - 1 && zin) {
-      const float4* c = sref + sxy + (int(threadIdx.y) + 1) * sx + (int(threadIdx.x) + 1);
-      // One load per direction: a lane on an x face takes, for the five
-      // directions that come from outside, the periodic wrap (the upwind
-      // reference is staged wrapped) or the halfway bounce-back from its own
-      // opposite population (decoded with its own reference: the term of
-      // opp(q) is w_q (dr - e_q.v)) plus the lid term.
+    if (y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1) {
+      // One population and one reference load per direction: a lane on an x
+      // face takes, for the five directions that come from outside, the
+      // periodic wrap or the halfway bounce-back from its own opposite
+      // population, decoded with its own reference (the term of opp(q) is
+      // w_q (dr - e_q.v)), plus the lid term -- a select of the addresses,
+      // so that every lane issues the same loads.
       const bool fl = x == 0, fr = x == a.nx - 1;
       const int kl = a.facebits & 3, kr = (a.facebits >> 2) & 3;
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         const __half* pq = a.srcq[q] + i;
-        float4 t = c[-cz(q) * sxy - cy(q) * sx - cx(q)];
+        const uint2* rq = r.refq[q] + i;
         float sgn = 1.0f, extra = 0.0f;
         if ((cx(q) == 1 && fl) || (cx(q) == -1 && fr)) {
           const int k = cx(q) == 1 ? kl : kr;
           if (k == BC_PERIODIC) {
             pq += cx(q) == 1 ? a.nx : -a.nx;
+            rq += cx(q) == 1 ? a.nx : -a.nx;
           } else {
             pq = a.src + int64_t(opp(q)) * a.qstride + i;
-            t = c[0];
+            rq = r.ref_src + i;
             sgn = -1.0f;
             extra = k == BC_LID ? a.lidc[q] : 0.0f;
           }
         }
-        const float ev = float(cx(q)) * t.y + float(cy(q)) * t.z + float(cz(q)) * t.w;
-        d[q] = dec16(*pq) + wt<float>(q) * (t.x + sgn * ev) + extra;
+        const Ref4 t = ref_load(rq);
+        const float ev = float(cx(q)) * t.vx + float(cy(q)) * t.vy + float(cz(q)) * t.vz;
+        d[q] = dec16(*pq) + wt<float>(q) * (t.dr + sgn * ev) + extra;
       }
     } else {
       pull_face_ref(a.src, r.ref_src, a.qstride, a.nx, a.ny, a.nz, a.pitch, a.plane, a.facebits,
@@ -391,36 +353,9 @@ void lid_table(const Geom& g, float* out) {
 
 // One node of the batched step in the F16R form: the same pull, references
 // and collision as step_ref_kernel.
-__device__ void ref_stage_batch(const LatDesc<float>& L, int parity, int x0, int y0, int z,
-                                int tw, int th, int lin, int twl, float4* sref) {
-  const uint2* rs = static_cast<const uint2*>(L.ref[parity]);
-  const int sx = tw + 2, sxy = sx * (th + 2);
-  const int lx = lin & (tw - 1), ly = lin >> twl;
-  const bool xper = (L.facebits & 3u) == unsigned(BC_PERIODIC);
-  for (int ky = ly; ky < th + 2; ky += th) {
-    const int gy = y0 - 1 + ky;
-    for (int kx = lx; kx < sx; kx += tw) {
-      int gx = x0 - 1 + kx;
-      if (xper) gx = gx == -1 ? L.nx - 1 : gx == L.nx ? 0 : gx;
-      const bool in = gx >= 0 && gx < L.nx && gy >= 0 && gy < L.ny;
-      const int gi = (z - 1) * L.plane + gy * L.pitch + gx;
-#pragma unroll
-      for (int kz = 0; kz < 3; ++kz) {
-        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (in) {
-          const Ref4 t = ref_load(rs + gi + kz * L.plane);
-          v = make_float4(t.dr, t.vx, t.vy, t.vz);
-        }
-        sref[kz * sxy + ky * sx + kx] = v;
-      }
-    }
-  }
-}
-
 template <bool FORCE>
 __device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y, int z,
-                               unsigned step, NodeOut<float>& o, const float4* sref, int sx,
-                               int sxy) {
+                               unsigned step, NodeOut<float>& o) {
   const __half* src = static_cast<const __half*>(L.buf[parity]);
   __half* dst = static_cast<__half*>(const_cast<void*>(L.buf[parity ^ 1]));
   const uint2* rs = static_cast<const uint2*>(L.ref[parity]);
@@ -430,27 +365,30 @@ __device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y
   const int i = z * plane + y * pitch + x;
   float d[Q];
   if (y > 0 && y < L.ny - 1 && z > 0 && z < L.nz - 1) {
-    // as in step_ref_kernel: one load per direction, x faces by a select
+    // as in step_ref_kernel: one load of each kind per direction, x faces
+    // by a select
     const bool fl = x == 0, fr = x == L.nx - 1;
     const int kl = L.facebits & 3, kr = (L.facebits >> 2) & 3;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      int j = q * qs + i - (cz(q) * plane + cy(q) * pitch + cx(q));
-      float4 t = sref[-cz(q) * sxy - cy(q) * sx - cx(q)];
+      const int up = i - (cz(q) * plane + cy(q) * pitch + cx(q));
+      int j = q * qs + up, jr = up;
       float sgn = 1.0f, extra = 0.0f;
       if ((cx(q) == 1 && fl) || (cx(q) == -1 && fr)) {
         const int k = cx(q) == 1 ? kl : kr;
         if (k == BC_PERIODIC) {
           j += cx(q) == 1 ? L.nx : -L.nx;
+          jr += cx(q) == 1 ? L.nx : -L.nx;
         } else {
           j = opp(q) * qs + i;
-          t = sref[0];
+          jr = i;
           sgn = -1.0f;
           extra = k == BC_LID ? L.lidc[q] : 0.0f;
         }
       }
-      const float ev = float(cx(q)) * t.y + float(cy(q)) * t.z + float(cz(q)) * t.w;
-      d[q] = dec16(src[j]) + wt<float>(q) * (t.x + sgn * ev) + extra;
+      const Ref4 t = ref_load(rs + jr);
+      const float ev = float(cx(q)) * t.vx + float(cy(q)) * t.vy + float(cz(q)) * t.vz;
+      d[q] = dec16(src[j]) + wt<float>(q) * (t.dr + sgn * ev) + extra;
     }
   } else {
     pull_face_ref(src, rs, L.qstride, L.nx, L.ny, L.nz, pitch, plane, L.facebits, x, y, z, i,
@@ -495,11 +433,10 @@ cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, vo
   const bool cap = (npt & 4) != 0;
   dim3 grid((g.nx + block.x - 1) / block.x, (g.ny + block.y - 1) / block.y, g.nz);
   cudaError_t e_ = cudaSuccess;
-  const size_t smem = ref_stage_bytes(int(block.x), int(block.y));
 #define CLBM_REF_LAUNCH(F, C_)                                                                  \
   do {                                                                                         \
-    if (cap) e_ = pdl_launch_smem(step_ref_kernel<F, C_, true>, grid, block, smem, st, a, r);  \
-    else e_ = pdl_launch_smem(step_ref_kernel<F, C_, false>, grid, block, smem, st, a, r);     \
+    if (cap) e_ = pdl_launch(step_ref_kernel<F, C_, true>, grid, block, st, a, r);            \
+    else e_ = pdl_launch(step_ref_kernel<F, C_, false>, grid, block, st, a, r);               \
   } while (0)
   if (P.has_force) {
     if (check) CLBM_REF_LAUNCH(true, true);
