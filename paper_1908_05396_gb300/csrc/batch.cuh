@@ -272,7 +272,7 @@ void fill_desc_t(void* out, double lam, const Geom& g, const PhysParams& P, cons
                           const void* other, const void* ref_cur, const void* ref_other,       \
                           void* uprev, int tx, int ty, int twl, int slot, unsigned so) {       \
     /* the F16R form carries unscaled deviations; FP16-shifted ones are scaled */            \
-    fill_desc_t<R>(out, REF ? 1.0 : double(1 << log2_scale<S>()), g, P, cur, other, ref_cur,   \
+    fill_desc_t<R>(out, double(1 << log2_scale<S>()), g, P, cur, other, ref_cur,             \
                    ref_other, uprev, tx, ty, twl, slot, so);                                   \
   }                                                                                            \
   cudaError_t upload_desc_##SUFFIX(const void* host, int base, int n) {                        \

@@ -695,7 +695,7 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
     clbm_ctx* h = b->slots[s];
     if (!h) continue;
     const size_t bytes = size_t(NQ) * size_t(h->g.qstride) * h->elem;
-    const size_t rbytes = h->ref[0] ? (size_t(h->g.plane) * h->g.nz + 64) * 8 : 0;
+    const size_t rbytes = h->ref[0] ? f16r_ref_bytes(h->g.plane * h->g.nz) : 0;
     err = cudaMallocAsync(&saved[s], bytes + rbytes, b->stream);
     if (err == cudaSuccess)
       err = cudaMemcpyAsync(saved[s], h->buf[h->cur], bytes, cudaMemcpyDeviceToDevice, b->stream);
@@ -814,7 +814,7 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
     h->layout = lay0[s];
     h->steps = steps0[s];
     const size_t bytes = size_t(NQ) * size_t(h->g.qstride) * h->elem;
-    const size_t rbytes = h->ref[0] ? (size_t(h->g.plane) * h->g.nz + 64) * 8 : 0;
+    const size_t rbytes = h->ref[0] ? f16r_ref_bytes(h->g.plane * h->g.nz) : 0;
     cudaError_t e2 = cudaMemcpyAsync(h->buf[h->cur], saved[s], bytes, cudaMemcpyDeviceToDevice,
                                      b->stream);
     if (e2 == cudaSuccess && rbytes)

@@ -219,7 +219,7 @@ int clbm_create(const clbm_domain* d, double K, double n, const double U_lid[3],
     rc = dev_alloc(h, &h->buf[b], pop_bytes, "population buffer");
   if (rc != CLBM_OK) return cleanup(rc, "clbm_create");
   if (dtype == CLBM_F16R) {
-    h->ref_bytes = (size_t(g.plane) * g.nz + 64) * 8;  // 4 halves per node, + slack
+    h->ref_bytes = f16r_ref_bytes(g.plane * g.nz);
     for (int b = 0; b < 2 && rc == CLBM_OK; ++b) {
       rc = dev_alloc(h, &h->ref[b], h->ref_bytes, "reference buffer");
       if (rc == CLBM_OK && cudaMemsetAsync(h->ref[b], 0, h->ref_bytes, h->stream) != cudaSuccess)
@@ -492,7 +492,7 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
     for (int v = 0; v < TMA_NVAR; ++v) cands.push_back({tma_bx(v), tma_by(v), TMA_NPT + 32 * v});
   // Save the state: tuning runs real steps.
   const size_t pop_bytes = size_t(NQ) * size_t(h->g.qstride) * h->elem;
-  const size_t ref_bytes = h->ref[0] ? (size_t(h->g.plane) * h->g.nz + 64) * 8 : 0;
+  const size_t ref_bytes = h->ref[0] ? f16r_ref_bytes(h->g.plane * h->g.nz) : 0;
   void* saved = nullptr;
   CK(h, cudaMallocAsync(&saved, pop_bytes + ref_bytes, h->stream));
   CK(h, cudaMemcpyAsync(saved, h->buf[h->cur], pop_bytes, cudaMemcpyDeviceToDevice, h->stream));

@@ -106,7 +106,7 @@ double lattice_bytes(clbm_dtype t, const clbm_domain& d) {
   const int64_t pitch = (d.nx + per_row - 1) / per_row * per_row;
   const int64_t plane = pitch * d.ny;
   const int64_t qs = (plane * d.nz + 255) / 256 * 256;
-  const int64_t refs = t == CLBM_F16R ? 2 * (plane * d.nz + 64) * 8 : 0;  // F16R references
+  const int64_t refs = t == CLBM_F16R ? int64_t(2 * clbm::f16r_ref_bytes(plane * d.nz)) : 0;
   return double(2 * 19 * qs * elem + 3 * plane * d.nz * rs + refs + 4096);
 }
 

@@ -1,57 +1,57 @@
 // step_f16r.cu -- kernels of the F16R storage form: FP16 populations stored
 // relative to the writing node's first-order equilibrium.
 //
-// Each node keeps a reference (rho - rho0, 3 rho u) of its last collision as
-// four FP16 values next to its populations, and stores
-//     s_q = fp16( 1024 * ( f~_q - w_q rho0 - r_q ) ),
-//     r_q = w_q [ drho + e_q . v ],  v = 3 (rho0 + drho) u  (reference values),
+// The deviations are carried scaled by lam = 1024 (as in the F16S form, with
+// the factor folded into the collision's constants).  Each node keeps a
+// reference (lam (rho - rho0), lam 3 rho u) of its last collision as one FP32
+// float4 next to its populations, and stores
+//     s_q = fp16( lam ( f~_q - w_q rho0 ) - r_q ),
+//     r_q = w_q [ dr + e_q . v ],  (dr, v) the reference,
 // which removes the rest value and the first-order (velocity) part of the
 // equilibrium, the largest parts of f~, before FP16 rounding (stochastic in
-// the step kernels, see enc16_sr2).  A reader
-// decodes with the reference of the node that wrote the value: the upwind
-// neighbour for a streamed value, itself for a bounced one.  Both sides use
-// the reference exactly as stored (rounded to FP16), so the encoding is
-// exactly invertible up to the FP16 rounding of the small remainder.
+// the step kernels, see enc16_sr2).  A reader decodes with the reference of
+// the node that wrote the value: the upwind neighbour for a streamed value,
+// itself for a bounced one.  Both sides use the reference exactly as stored,
+// so decoding undoes the encoding up to the FP16 rounding of the small
+// remainder (and one FP32 rounding).  A reference is read once per direction
+// by 19 readers, so it is kept in FP32: one 128-bit load with no conversions.
 // The reference arrays are double-buffered with the populations.
 #include "batch.cuh"
 
 namespace clbm {
 namespace {
 
+constexpr int LOG2LAM = 10;  // log2 of the scale of the carried deviations
+constexpr float LAM = float(1 << LOG2LAM);
+static_assert(double(1 << LOG2LAM) == F16_SCALE, "one FP16 storage scale");
+
 struct Ref4 {
-  float dr, vx, vy, vz;  // rho - rho0 and v = 3 rho u, as stored (FP16)
+  float dr, vx, vy, vz;  // lam (rho - rho0) and v = lam 3 rho u
 };
 
-__device__ __forceinline__ Ref4 ref_load(const uint2* p) {
-  const uint2 v = *p;
-  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
-  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
-  return {a.x, a.y, b.x, b.y};
+__device__ __forceinline__ Ref4 ref_load(const float4* p) {
+  const float4 v = *p;
+  return {v.x, v.y, v.z, v.w};
 }
 
-// Round (drho, 3 rho u) to FP16 for storage; r receives the rounded values.
-__device__ __forceinline__ uint2 ref_pack(float dr, float ux, float uy, float uz, float rho0,
-                                          Ref4& r) {
-  const float r3 = 3.0f * (rho0 + dr);
-  const __half2 a = __floats2half2_rn(dr, r3 * ux), b = __floats2half2_rn(r3 * uy, r3 * uz);
-  const float2 fa = __half22float2(a), fb = __half22float2(b);
-  r = {fa.x, fa.y, fb.x, fb.y};
-  uint2 v;
-  v.x = *reinterpret_cast<const unsigned*>(&a);
-  v.y = *reinterpret_cast<const unsigned*>(&b);
-  return v;
+// The reference of a node with density rho = rho0 + drho and velocity u.
+__device__ __forceinline__ float4 ref_make(float drho, float rho, float ux, float uy, float uz,
+                                           Ref4& r) {
+  const float r3 = (3.0f * LAM) * rho;
+  r = {LAM * drho, r3 * ux, r3 * uy, r3 * uz};
+  return make_float4(r.dr, r.vx, r.vy, r.vz);
 }
 
 // First-order equilibrium deviation of direction q about the reference,
-// w_q [drho + 3 rho (e_q . u)]: the stored v = 3 rho u saves the product per
-// direction (rho0 is carried in v).
-__device__ __forceinline__ float ref_term(int q, const Ref4& r, float /*rho0*/) {
+// lam w_q [drho + 3 rho (e_q . u)]: the stored v = lam 3 rho u saves the
+// product per direction.
+__device__ __forceinline__ float ref_term(int q, const Ref4& r) {
   const float ev = float(cx(q)) * r.vx + float(cy(q)) * r.vy + float(cz(q)) * r.vz;
   return wt<float>(q) * (r.dr + ev);
 }
 
-__device__ __forceinline__ float dec16(__half v) { return __half2float(v) * float(1.0 / F16_SCALE); }
-__device__ __forceinline__ __half enc16(float v) { return __float2half_rn(v * float(F16_SCALE)); }
+__device__ __forceinline__ float dec16(__half v) { return __half2float(v); }
+__device__ __forceinline__ __half enc16(float v) { return __float2half_rn(v); }
 
 // Stochastic rounding of the stores: a value is rounded up in magnitude with
 // probability equal to the fraction of an FP16 ulp it carries, so increments
@@ -87,7 +87,7 @@ __device__ __forceinline__ void enc16_sr2(float a, float b, uint32_t& state, __h
   uint32_t d;
   asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;"
       : "=r"(d)
-      : "f"(a * float(F16_SCALE)), "f"(b * float(F16_SCALE)), "r"(rbits));
+      : "f"(a), "f"(b), "r"(rbits));
   hi = __ushort_as_half(static_cast<unsigned short>(d >> 16));
   lo = __ushort_as_half(static_cast<unsigned short>(d & 0xFFFFu));
 }
@@ -96,11 +96,11 @@ __device__ __forceinline__ void enc16_sr2(float a, float b, uint32_t& state, __h
 // two directions per conversion.
 template <typename Dst>
 __device__ __forceinline__ void store_sr(Dst&& dst_q, const float (&d)[Q], const Ref4& rr,
-                                         float rho0, uint32_t state) {
+                                         uint32_t state) {
 #pragma unroll
   for (int q = 0; q < Q; q += 2) {
-    const float a = d[q] - ref_term(q, rr, rho0);
-    const float b = q + 1 < Q ? d[q + 1] - ref_term(q + 1 < Q ? q + 1 : q, rr, rho0) : 0.0f;
+    const float a = d[q] - ref_term(q, rr);
+    const float b = q + 1 < Q ? d[q + 1] - ref_term(q + 1 < Q ? q + 1 : q, rr) : 0.0f;
     __half hi, lo;
     enc16_sr2(a, b, state, hi, lo);
     dst_q(q) = hi;
@@ -109,9 +109,9 @@ __device__ __forceinline__ void store_sr(Dst&& dst_q, const float (&d)[Q], const
 }
 
 struct RefArgs {
-  const uint2* refq[Q];  // refq[q][i]: reference of the upwind neighbour of node i
-  const uint2* ref_src;  // references of the source step
-  uint2* ref_dst;        // references written by this step
+  const float4* refq[Q];  // refq[q][i]: reference of the upwind neighbour of node i
+  const float4* ref_src;  // references of the source step
+  float4* ref_dst;        // references written by this step
   unsigned step;         // the lattice's steps done before this one
 };
 
@@ -120,10 +120,10 @@ struct RefArgs {
 // reference of the node that wrote it: the upwind (or wrapped) node for a
 // streamed value, the node itself for a bounced one.
 __device__ __forceinline__ void pull_face_ref(const __half* __restrict__ src,
-                                              const uint2* __restrict__ ref, int64_t qstride,
+                                              const float4* __restrict__ ref, int64_t qstride,
                                               int nx, int ny, int nz, int pitch, int plane,
                                               unsigned fb, int x, int y, int z, int i,
-                                              const float* lidc, float rho0, float (&d)[Q]) {
+                                              const float* lidc, float (&d)[Q]) {
   const bool fx0 = x == 0, fx1 = x == nx - 1, fy0 = y == 0, fy1 = y == ny - 1;
   const bool fz0 = z == 0, fz1 = z == nz - 1;
 #pragma unroll
@@ -134,7 +134,7 @@ __device__ __forceinline__ void pull_face_ref(const __half* __restrict__ src,
     const bool oz = (cz(q) == 1 && fz0) || (cz(q) == -1 && fz1);
     const int up = i - (cz(q) * plane + cy(q) * pitch + cx(q));
     if (!(ox || oy || oz)) {
-      d[q] = dec16(sq[up]) + ref_term(q, ref_load(ref + up), rho0);
+      d[q] = dec16(sq[up]) + ref_term(q, ref_load(ref + up));
       continue;
     }
     const int kx = ox ? int((fb >> (cx(q) == 1 ? 0 : 2)) & 3u) : int(BC_PERIODIC);
@@ -143,14 +143,14 @@ __device__ __forceinline__ void pull_face_ref(const __half* __restrict__ src,
     if (kx != BC_PERIODIC || ky != BC_PERIODIC || kz != BC_PERIODIC) {
       const bool lid = kx == BC_LID || ky == BC_LID || kz == BC_LID;
       const float v = dec16(src[int64_t(opp(q)) * qstride + i]) +
-                      ref_term(opp(q), ref_load(ref + i), rho0);
+                      ref_term(opp(q), ref_load(ref + i));
       d[q] = lid ? v + lidc[q] : v;
     } else {
       int j = up;
       if (ox) j += cx(q) == 1 ? nx : -nx;
       if (oy) j += cy(q) == 1 ? ny * pitch : -ny * pitch;
       if (oz) j += cz(q) == 1 ? nz * plane : -nz * plane;
-      d[q] = dec16(sq[j]) + ref_term(q, ref_load(ref + j), rho0);
+      d[q] = dec16(sq[j]) + ref_term(q, ref_load(ref + j));
     }
   }
 }
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         const __half* pq = a.srcq[q] + i;
-        const uint2* rq = r.refq[q] + i;
+        const float4* rq = r.refq[q] + i;
         float sgn = 1.0f, extra = 0.0f;
         if ((cx(q) == 1 && fl) || (cx(q) == -1 && fr)) {
           const int k = cx(q) == 1 ? kl : kr;
@@ -202,14 +202,13 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
       }
     } else {
       pull_face_ref(a.src, r.ref_src, a.qstride, a.nx, a.ny, a.nz, a.pitch, a.plane, a.facebits,
-                    x, y, z, i, a.lidc, rho0, d);
+                    x, y, z, i, a.lidc, d);
     }
     NodeOut<float> o;
-    collide<float, FORCE>(a.C, d, o);
+    collide<float, FORCE, false, LOG2LAM>(a.C, d, o);
     Ref4 rr;
-    r.ref_dst[i] = ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rho0, rr);
-    store_sr([&](int q) -> __half& { return a.dstq[q][i]; }, d, rr, rho0,
-             sr_seed(uint32_t(i), r.step));
+    r.ref_dst[i] = ref_make(o.rho - rho0, o.rho, o.ux, o.uy, o.uz, rr);
+    store_sr([&](int q) -> __half& { return a.dstq[q][i]; }, d, rr, sr_seed(uint32_t(i), r.step));
     if (CHECK) {
       float* up = reinterpret_cast<float*>(a.cb.uprev);
       const int64_t nst = int64_t(a.plane) * a.nz;
@@ -237,7 +236,7 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
 
 template <bool FORCE>
 __global__ void __launch_bounds__(256) fields_ref_kernel(const __half* __restrict__ src,
-                                                         const uint2* __restrict__ ref, Geom g,
+                                                         const float4* __restrict__ ref, Geom g,
                                                          CollideConst<float> C,
                                                          const float* __restrict__ lidc,
                                                          double* rho, double* u, double* gd) {
@@ -248,9 +247,9 @@ __global__ void __launch_bounds__(256) fields_ref_kernel(const __half* __restric
   const int i = z * int(g.plane) + y * g.pitch + x;
   float d[Q];
   pull_face_ref(src, ref, g.qstride, g.nx, g.ny, g.nz, g.pitch, int(g.plane), g.facebits, x, y,
-                z, i, lidc, C.rho0, d);
+                z, i, lidc, d);
   NodeOut<float> o;
-  collide<float, FORCE>(C, d, o);
+  collide<float, FORCE, false, LOG2LAM>(C, d, o);
   const int64_t N = int64_t(g.nx) * g.ny * g.nz;
   const int64_t k = (int64_t(z) * g.ny + y) * g.nx + x;
   if (rho) rho[k] = double(o.rho);
@@ -262,7 +261,7 @@ __global__ void __launch_bounds__(256) fields_ref_kernel(const __half* __restric
   if (gd) gd[k] = double(o.gamma_dot);
 }
 
-__global__ void export_ref_kernel(const __half* __restrict__ src, const uint2* __restrict__ ref,
+__global__ void export_ref_kernel(const __half* __restrict__ src, const float4* __restrict__ ref,
                                   Geom g, float rho0, double* __restrict__ out) {
   const int64_t N = int64_t(g.nx) * g.ny * g.nz;
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -271,14 +270,14 @@ __global__ void export_ref_kernel(const __half* __restrict__ src, const uint2* _
   const int64_t k = t - int64_t(q) * N;
   const int x = int(k % g.nx), y = int((k / g.nx) % g.ny), z = int(k / (int64_t(g.nx) * g.ny));
   const int64_t i = int64_t(z) * g.plane + int64_t(y) * g.pitch + x;
-  const float dev = dec16(src[q * g.qstride + i]) + ref_term(q, ref_load(ref + i), rho0);
-  out[t] = double(dev) + wt<double>(q) * double(rho0);
+  const float dev = dec16(src[q * g.qstride + i]) + ref_term(q, ref_load(ref + i));
+  out[t] = double(dev) * (1.0 / double(LAM)) + wt<double>(q) * double(rho0);
 }
 
 // One thread per node: the reference is the node's own moments of the
 // imported populations.
 __global__ void import_ref_kernel(const double* __restrict__ in, Geom g, float rho0,
-                                  __half* __restrict__ dst, uint2* __restrict__ ref) {
+                                  __half* __restrict__ dst, float4* __restrict__ ref) {
   const int64_t N = int64_t(g.nx) * g.ny * g.nz;
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -294,11 +293,12 @@ __global__ void import_ref_kernel(const double* __restrict__ in, Geom g, float r
     jz += cz(q) * f[q];
   }
   Ref4 rr;
-  ref[i] = ref_pack(float(rho - rho0), float(jx / rho), float(jy / rho), float(jz / rho), rho0, rr);
+  ref[i] = ref_make(float(rho - rho0), float(rho), float(jx / rho), float(jy / rho),
+                    float(jz / rho), rr);
 #pragma unroll
   for (int q = 0; q < Q; ++q)
     dst[q * g.qstride + i] =
-        enc16(float(f[q] - wt<double>(q) * rho0) - ref_term(q, rr, rho0));
+        enc16(float((f[q] - wt<double>(q) * rho0) * double(LAM)) - ref_term(q, rr));
 }
 
 // M independent nodes: store (with its own reference), load, collide, store
@@ -320,20 +320,21 @@ __global__ void collide_nodes_ref_kernel(CollideConst<float> C, const double* __
     jz += cz(q) * v;
   }
   Ref4 rr;
-  ref_pack(float(r0 - rho0), float(jx / r0), float(jy / r0), float(jz / r0), rho0, rr);
+  ref_make(float(r0 - rho0), float(r0), float(jx / r0), float(jy / r0), float(jz / r0), rr);
   float d[Q];
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    const float t = ref_term(q, rr, rho0);
-    d[q] = dec16(enc16(float(fin[q * M + k] - wt<double>(q) * rho0) - t)) + t;
+    const float t = ref_term(q, rr);
+    d[q] = dec16(enc16(float((fin[q * M + k] - wt<double>(q) * rho0) * double(LAM)) - t)) + t;
   }
   NodeOut<float> o;
-  collide<float, FORCE>(C, d, o);
-  ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rho0, rr);
+  collide<float, FORCE, false, LOG2LAM>(C, d, o);
+  ref_make(o.rho - rho0, o.rho, o.ux, o.uy, o.uz, rr);
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    const float t = ref_term(q, rr, rho0);
-    fout[q * M + k] = double(dec16(enc16(d[q] - t)) + t) + wt<double>(q) * double(rho0);
+    const float t = ref_term(q, rr);
+    fout[q * M + k] = double(dec16(enc16(d[q] - t)) + t) * (1.0 / double(LAM)) +
+                      wt<double>(q) * double(rho0);
   }
   if (rho) rho[k] = double(o.rho);
   if (u) {
@@ -344,9 +345,11 @@ __global__ void collide_nodes_ref_kernel(CollideConst<float> C, const double* __
   if (gd) gd[k] = double(o.gamma_dot);
 }
 
+// Lid terms of the bounce-back, in the scaled deviations.
 void lid_table(const Geom& g, float* out) {
   for (int q = 0; q < Q; ++q)
-    out[q] = float(6.0 * wt<double>(q) * g.rho0 * (cx(q) * g.U[0] + cy(q) * g.U[1] + cz(q) * g.U[2]));
+    out[q] = float(6.0 * double(LAM) * wt<double>(q) * g.rho0 *
+                   (cx(q) * g.U[0] + cy(q) * g.U[1] + cz(q) * g.U[2]));
 }
 
 }  // namespace
@@ -358,8 +361,8 @@ __device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y
                                unsigned step, NodeOut<float>& o) {
   const __half* src = static_cast<const __half*>(L.buf[parity]);
   __half* dst = static_cast<__half*>(const_cast<void*>(L.buf[parity ^ 1]));
-  const uint2* rs = static_cast<const uint2*>(L.ref[parity]);
-  uint2* rd = static_cast<uint2*>(const_cast<void*>(L.ref[parity ^ 1]));
+  const float4* rs = static_cast<const float4*>(L.ref[parity]);
+  float4* rd = static_cast<float4*>(const_cast<void*>(L.ref[parity ^ 1]));
   const float rho0 = L.C.rho0;
   const int qs = int(L.qstride), plane = L.plane, pitch = L.pitch;
   const int i = z * plane + y * pitch + x;
@@ -392,12 +395,12 @@ __device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y
     }
   } else {
     pull_face_ref(src, rs, L.qstride, L.nx, L.ny, L.nz, pitch, plane, L.facebits, x, y, z, i,
-                  L.lidc, rho0, d);
+                  L.lidc, d);
   }
-  collide<float, FORCE>(L.C, d, o);
+  collide<float, FORCE, false, LOG2LAM>(L.C, d, o);
   Ref4 rr;
-  rd[i] = ref_pack(o.rho - rho0, o.ux, o.uy, o.uz, rho0, rr);
-  store_sr([&](int q) -> __half& { return dst[q * qs + i]; }, d, rr, rho0, sr_seed(uint32_t(i), step));
+  rd[i] = ref_make(o.rho - rho0, o.rho, o.ux, o.uy, o.uz, rr);
+  store_sr([&](int q) -> __half& { return dst[q * qs + i]; }, d, rr, sr_seed(uint32_t(i), step));
 }
 
 cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, void* ref_dst,
@@ -408,17 +411,18 @@ cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, vo
   r.step = unsigned(uint64_t(step));
   const __half* s = static_cast<const __half*>(src);
   __half* d = static_cast<__half*>(dst);
-  const uint2* rs = static_cast<const uint2*>(ref_src);
+  const float4* rs = static_cast<const float4*>(ref_src);
   for (int q = 0; q < Q; ++q) {
     const int64_t off = int64_t(cz(q)) * g.plane + int64_t(cy(q)) * g.pitch + cx(q);
     a.srcq[q] = reinterpret_cast<const __half*>(reinterpret_cast<uintptr_t>(s) +
                                                  (int64_t(q) * g.qstride - off) * 2);
     a.dstq[q] = d + int64_t(q) * g.qstride;
-    r.refq[q] = reinterpret_cast<const uint2*>(reinterpret_cast<uintptr_t>(rs) - off * 8);
+    r.refq[q] = reinterpret_cast<const float4*>(reinterpret_cast<uintptr_t>(rs) -
+                                                 off * int64_t(sizeof(float4)));
   }
   lid_table(g, a.lidc);
   r.ref_src = rs;
-  r.ref_dst = static_cast<uint2*>(ref_dst);
+  r.ref_dst = static_cast<float4*>(ref_dst);
   a.zrev = reinterpret_cast<uintptr_t>(dst) < reinterpret_cast<uintptr_t>(src) ? 1 : 0;
   a.src = s;
   a.qstride = g.qstride;
@@ -428,7 +432,7 @@ cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, vo
   a.pitch = g.pitch;
   a.plane = int(g.plane);
   a.facebits = g.facebits;
-  a.C = make_const<float>(P);
+  a.C = make_const<float>(P, double(LAM));
   a.cb = cb;
   const bool cap = (npt & 4) != 0;
   dim3 grid((g.nx + block.x - 1) / block.x, (g.ny + block.y - 1) / block.y, g.nz);
@@ -461,9 +465,9 @@ cudaError_t launch_fields_f16r(const void* src, const void* ref, const Geom& g,
   if (e == cudaSuccess) {
     dim3 block(32, 4);
     dim3 grid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz);
-    const CollideConst<float> C = make_const<float>(P);
+    const CollideConst<float> C = make_const<float>(P, double(LAM));
     const __half* s = static_cast<const __half*>(src);
-    const uint2* r = static_cast<const uint2*>(ref);
+    const float4* r = static_cast<const float4*>(ref);
     if (P.has_force) fields_ref_kernel<true><<<grid, block, 0, st>>>(s, r, g, C, dlid, rho, u, gd);
     else fields_ref_kernel<false><<<grid, block, 0, st>>>(s, r, g, C, dlid, rho, u, gd);
     e = cudaGetLastError();
@@ -477,7 +481,7 @@ cudaError_t launch_export_f16r(const void* src, const void* ref, const Geom& g, 
   const int64_t total = int64_t(g.nx) * g.ny * g.nz * Q;
   const int b = 256;
   export_ref_kernel<<<unsigned((total + b - 1) / b), b, 0, st>>>(
-      static_cast<const __half*>(src), static_cast<const uint2*>(ref), g, float(rho0), out);
+      static_cast<const __half*>(src), static_cast<const float4*>(ref), g, float(rho0), out);
   return cudaGetLastError();
 }
 
@@ -487,7 +491,7 @@ cudaError_t launch_import_f16r(const double* in, const Geom& g, double rho0, voi
   const int b = 128;
   import_ref_kernel<<<unsigned((N + b - 1) / b), b, 0, st>>>(in, g, float(rho0),
                                                               static_cast<__half*>(dst),
-                                                              static_cast<uint2*>(ref));
+                                                              static_cast<float4*>(ref));
   return cudaGetLastError();
 }
 
@@ -496,7 +500,7 @@ cudaError_t launch_collide_nodes_f16r(const PhysParams& P, const double* fin, do
                                       cudaStream_t st) {
   const int b = 128;
   const unsigned grid = unsigned((M + b - 1) / b);
-  const CollideConst<float> C = make_const<float>(P);
+  const CollideConst<float> C = make_const<float>(P, double(LAM));
   if (P.has_force) collide_nodes_ref_kernel<true><<<grid, b, 0, st>>>(C, fin, fout, rho, u, gd, M);
   else collide_nodes_ref_kernel<false><<<grid, b, 0, st>>>(C, fin, fout, rho, u, gd, M);
   return cudaGetLastError();
