@@ -21,6 +21,12 @@
 namespace clbm {
 namespace {
 
+// The back-transform of the collision: unforced, the populations are rebuilt
+// from the pair values (the inputs die early, which frees registers; the FP16
+// rounding noise of the stores lies far above the FP32 roundings of the
+// rebuild); with a body force, one correction per population, which keeps a
+// weak force's increments to one rounding (rebuilt from the pairs, a forced
+// channel's velocity drifted by 1e-3 against FP64).
 constexpr int LOG2LAM = 10;  // log2 of the scale of the carried deviations
 constexpr float LAM = float(1 << LOG2LAM);
 static_assert(double(1 << LOG2LAM) == F16_SCALE, "one FP16 storage scale");
@@ -205,7 +211,7 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
                     x, y, z, i, a.lidc, d);
     }
     NodeOut<float> o;
-    collide<float, FORCE, false, LOG2LAM>(a.C, d, o);
+    collide<float, FORCE, !FORCE, LOG2LAM>(a.C, d, o);
     Ref4 rr;
     r.ref_dst[i] = ref_make(o.rho - rho0, o.rho, o.ux, o.uy, o.uz, rr);
     store_sr([&](int q) -> __half& { return a.dstq[q][i]; }, d, rr, sr_seed(uint32_t(i), r.step));
@@ -249,7 +255,7 @@ __global__ void __launch_bounds__(256) fields_ref_kernel(const __half* __restric
   pull_face_ref(src, ref, g.qstride, g.nx, g.ny, g.nz, g.pitch, int(g.plane), g.facebits, x, y,
                 z, i, lidc, d);
   NodeOut<float> o;
-  collide<float, FORCE, false, LOG2LAM>(C, d, o);
+  collide<float, FORCE, !FORCE, LOG2LAM>(C, d, o);
   const int64_t N = int64_t(g.nx) * g.ny * g.nz;
   const int64_t k = (int64_t(z) * g.ny + y) * g.nx + x;
   if (rho) rho[k] = double(o.rho);
@@ -328,7 +334,7 @@ __global__ void collide_nodes_ref_kernel(CollideConst<float> C, const double* __
     d[q] = dec16(enc16(float((fin[q * M + k] - wt<double>(q) * rho0) * double(LAM)) - t)) + t;
   }
   NodeOut<float> o;
-  collide<float, FORCE, false, LOG2LAM>(C, d, o);
+  collide<float, FORCE, !FORCE, LOG2LAM>(C, d, o);
   ref_make(o.rho - rho0, o.rho, o.ux, o.uy, o.uz, rr);
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
@@ -397,7 +403,7 @@ __device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y
     pull_face_ref(src, rs, L.qstride, L.nx, L.ny, L.nz, pitch, plane, L.facebits, x, y, z, i,
                   L.lidc, d);
   }
-  collide<float, FORCE, false, LOG2LAM>(L.C, d, o);
+  collide<float, FORCE, !FORCE, LOG2LAM>(L.C, d, o);
   Ref4 rr;
   rd[i] = ref_make(o.rho - rho0, o.rho, o.ux, o.uy, o.uz, rr);
   store_sr([&](int q) -> __half& { return dst[q * qs + i]; }, d, rr, sr_seed(uint32_t(i), step));
