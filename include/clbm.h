@@ -202,9 +202,7 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
  * v = 4: 32x4, 1; v = 5: 64x2, 1; v = 6: 64x2, 2; v = 7: 32x4, 2; v = 8:
  * 64x2, 2 (four CTAs per SM); v = 9: 128x1, 2.  With two nodes a thread
  * collides rows 2y and 2y+1 as a packed FP32 pair.  block_x x block_y must
- * be that shape's.  F16R storage also takes npt + 256 k, k = 1, 2 or 3: each
- * block then steps 2^k consecutive z planes of its tile (CLBM_ERR_UNSUPPORTED
- * for the other forms).  Check steps run
+ * be that shape's.  Check steps run
  * the plain kernel with the same block.  If a pipeline wait of that kernel
  * gives up (about one second; never expected), the next check makes
  * clbm_step / clbm_residual return CLBM_ERR_CUDA. */

@@ -487,13 +487,6 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
   if (tw < 32)
     for (int capped = 0; capped <= 1; ++capped)
       for (int t : {64, 128, 256}) cands.push_back({tw, t / tw, 1 + 4 * capped});
-  // F16R: blocks that step 2, 4 or 8 consecutive z planes
-  if (h->dtype == CLBM_F16R && !h->in_place) {
-    const size_t n0 = cands.size();
-    for (int zl = 1; zl <= 3; ++zl)
-      for (size_t k = 0; k < n0; ++k)
-        if (cands[k].bx * cands[k].by >= 64) cands.push_back({cands[k].bx, cands[k].by, cands[k].npt + 256 * zl});
-  }
   // FP32 and FP16 storage: the TMA-staged kernel in each of its shapes
   if ((h->dtype == CLBM_F32 || h->dtype == CLBM_F16S) && !h->in_place)
     for (int v = 0; v < TMA_NVAR; ++v) cands.push_back({tma_bx(v), tma_by(v), TMA_NPT + 32 * v});
@@ -596,10 +589,8 @@ int clbm_set_launch(clbm_handle h, int block_x, int block_y, int npt) {
     return CLBM_OK;
   }
   const int np = npt & 3;
-  if ((np != 1 && np != 2) || (npt & ~(7 | 0x300)))
+  if ((np != 1 && np != 2) || (npt & ~7))
     return fail(h, CLBM_ERR_ARG, "npt must be 1 or 2, plus 4 for the register-capped kernel");
-  if ((npt & 0x300) && h->dtype != CLBM_F16R)
-    return fail(h, CLBM_ERR_UNSUPPORTED, "z planes per block (npt + 256 k) are an F16R launch");
   if (block_x < 1 || block_y < 1 || block_x * block_y > (np == 2 ? 128 : 256) ||
       block_x * block_y % 32 != 0)
     return fail(h, CLBM_ERR_ARG, "block must have a multiple of 32 threads, at most 256 "

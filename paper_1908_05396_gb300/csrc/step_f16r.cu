@@ -119,7 +119,6 @@ struct RefArgs {
   const float4* ref_src;  // references of the source step
   float4* ref_dst;        // references written by this step
   unsigned step;         // the lattice's steps done before this one
-  int zc;                // consecutive z planes per block
 };
 
 // Pull of all 19 directions into node (x, y, z) with index i, for a node on
@@ -162,24 +161,18 @@ __device__ __forceinline__ void pull_face_ref(const __half* __restrict__ src,
   }
 }
 
-// A block steps r.zc consecutive planes of its x-y tile, one after the
-// other: the references of plane z+1, read as upwind values of plane z, are
-// read again as plane z+1 collides and as upwind values of plane z+2, and
-// then come from L1 rather than L2 (each reference is read by 19 nodes).
 template <bool FORCE, bool CHECK, bool CAP>
 __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepArgs<__half, float> a,
                                                                     const RefArgs r) {
   pdl_enter();
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = a.zrev ? a.nz - 1 - int(blockIdx.z) : int(blockIdx.z);  // as step_kernel
   const bool active = x < a.nx && y < a.ny;
   if (!CHECK && !active) return;
   const float rho0 = a.C.rho0;
   double du2 = 0.0, uu = 0.0, dr = 0.0;
   int bad = 0;
-  const int zb = int(blockIdx.z) * r.zc, ze = min(zb + r.zc, a.nz);
-  for (int zz = zb; zz < ze; ++zz) {
-  const int z = a.zrev ? a.nz - 1 - zz : zz;  // as step_kernel
   if (active) {
     const int i = z * a.plane + y * a.pitch + x;
     float d[Q];
@@ -231,13 +224,12 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
       up[2 * nst + i] = o.uz;
       const double ex = double(o.ux) - double(px), ey = double(o.uy) - double(py),
                    ez = double(o.uz) - double(pz);
-      du2 += ex * ex + ey * ey + ez * ez;
-      uu += double(o.ux) * double(o.ux) + double(o.uy) * double(o.uy) + double(o.uz) * double(o.uz);
-      dr += double(o.rho) - double(rho0);
+      du2 = ex * ex + ey * ey + ez * ez;
+      uu = double(o.ux) * double(o.ux) + double(o.uy) * double(o.uy) + double(o.uz) * double(o.uz);
+      dr = double(o.rho) - double(rho0);
       const double chk = double(o.rho) + double(o.ux) + double(o.uy) + double(o.uz);
-      bad |= !(chk == chk) || !(fabs(chk) < 1e30) || !(double(o.rho) > 0.5 && double(o.rho) < 2.0);
+      bad = !(chk == chk) || !(fabs(chk) < 1e30) || !(double(o.rho) > 0.5 && double(o.rho) < 2.0);
     }
-  }
   }
   if (CHECK) {
     __shared__ double smem[32];
@@ -449,9 +441,7 @@ cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, vo
   a.C = make_const<float>(P, double(LAM));
   a.cb = cb;
   const bool cap = (npt & 4) != 0;
-  r.zc = 1 << ((npt >> 8) & 3);
-  dim3 grid((g.nx + block.x - 1) / block.x, (g.ny + block.y - 1) / block.y,
-            unsigned((g.nz + r.zc - 1) / r.zc));
+  dim3 grid((g.nx + block.x - 1) / block.x, (g.ny + block.y - 1) / block.y, g.nz);
   cudaError_t e_ = cudaSuccess;
 #define CLBM_REF_LAUNCH(F, C_)                                                                  \
   do {                                                                                         \

@@ -216,9 +216,7 @@ SHAPES = {"f64": [(32, 4, 1), (64, 2, 1), (128, 1, 1), (32, 8, 1)],
           "f32": [(32, 4, 1), (128, 2, 1), (32, 4, 2), (64, 2, 2), (128, 1, 2), (32, 2, 2)]
           + TMA_SHAPES,
           "f16s": [(32, 4, 1), (32, 4, 2), (64, 1, 2), (64, 4, 16), (32, 8, 80), (64, 2, 208)],
-          # F16R: + 256 k, blocks stepping 2^k consecutive z planes (9 planes: ragged)
-          "f16r": [(32, 4, 1), (64, 2, 5), (32, 8, 5), (32, 4, 5 + 256), (64, 2, 1 + 512),
-                   (32, 4, 5 + 768)]}
+          "f16r": [(32, 4, 1), (64, 2, 5), (32, 8, 5)]}
 
 
 @pytest.mark.parametrize("dtype,shape", [(d, s) for d in SHAPES for s in SHAPES[d]])
@@ -239,16 +237,6 @@ def test_ragged_mixed_boundaries_random_state(clbm, mixed_reference, dtype, shap
         assert l2 <= 1e-4
     else:
         assert l2 <= 2e-3
-
-
-def test_z_planes_per_block_is_an_f16r_launch(clbm):
-    with _lattice(clbm, _MIXED, "f32") as lat:
-        with pytest.raises(clbm.CLBMError):
-            lat.set_launch(32, 4, 1 + 256)
-    with _lattice(clbm, _MIXED, "f16r") as lat:
-        lat.set_launch(32, 4, 1 + 256)
-        with pytest.raises(clbm.CLBMError):
-            lat.set_launch(32, 4, 1 + 1024)
 
 
 def test_autotune_restores_state_and_keeps_parity(clbm):
