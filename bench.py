@@ -32,8 +32,8 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS & % HBM roofline, FP64 vs FP32/FP16-store; served solves/s, p50/p99"
 BYTES_PER_POP = {"f64": 8, "f32": 4, "f16s": 2, "f16r": 2}
 # algorithmic bytes per lattice update: 19 reads + 19 writes of the stored
-# type; F16R also reads and writes its node's 16-byte FP32 reference
-BYTES_PER_UPDATE = {"f64": 304, "f32": 152, "f16s": 76, "f16r": 108}
+# type; F16R also reads and writes its node's 8-byte FP16 reference
+BYTES_PER_UPDATE = {"f64": 304, "f32": 152, "f16s": 76, "f16r": 92}
 L_BENCH = 128
 RE_BENCH = 100.0
 NS_BENCH = (0.5, 1.0, 1.5)

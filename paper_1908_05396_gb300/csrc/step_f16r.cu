@@ -3,8 +3,8 @@
 //
 // The deviations are carried scaled by lam = 1024 (as in the F16S form, with
 // the factor folded into the collision's constants).  Each node keeps a
-// reference (lam (rho - rho0), lam 3 rho u) of its last collision as one FP32
-// float4 next to its populations, and stores
+// reference (lam (rho - rho0), lam 3 rho u) of its last collision as four
+// FP16 values next to its populations, and stores
 //     s_q = fp16( lam ( f~_q - w_q rho0 ) - r_q ),
 //     r_q = w_q [ dr + e_q . v ],  (dr, v) the reference,
 // which removes the rest value and the first-order (velocity) part of the
@@ -13,8 +13,9 @@
 // the node that wrote the value: the upwind neighbour for a streamed value,
 // itself for a bounced one.  Both sides use the reference exactly as stored,
 // so decoding undoes the encoding up to the FP16 rounding of the small
-// remainder (and one FP32 rounding).  A reference is read once per direction
-// by 19 readers, so it is kept in FP32: one 128-bit load with no conversions.
+// remainder (and one FP32 rounding).  A reference is read by 19 readers, one
+// 64-bit load each: in FP16 the 19 loads of a node need half the registers in
+// flight (and half the L1/L2 traffic) of FP32 references.
 // The reference arrays are double-buffered with the populations.
 #include "batch.cuh"
 
@@ -32,20 +33,28 @@ constexpr float LAM = float(1 << LOG2LAM);
 static_assert(double(1 << LOG2LAM) == F16_SCALE, "one FP16 storage scale");
 
 struct Ref4 {
-  float dr, vx, vy, vz;  // lam (rho - rho0) and v = lam 3 rho u
+  float dr, vx, vy, vz;  // lam (rho - rho0) and v = lam 3 rho u, as stored (FP16)
 };
 
-__device__ __forceinline__ Ref4 ref_load(const float4* p) {
-  const float4 v = *p;
-  return {v.x, v.y, v.z, v.w};
+__device__ __forceinline__ Ref4 ref_load(const uint2* p) {
+  const uint2 v = *p;
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+  return {a.x, a.y, b.x, b.y};
 }
 
-// The reference of a node with density rho = rho0 + drho and velocity u.
-__device__ __forceinline__ float4 ref_make(float drho, float rho, float ux, float uy, float uz,
-                                           Ref4& r) {
+// The reference of a node with density rho = rho0 + drho and velocity u,
+// rounded to FP16 for storage; r receives the rounded values.
+__device__ __forceinline__ uint2 ref_make(float drho, float rho, float ux, float uy, float uz,
+                                          Ref4& r) {
   const float r3 = (3.0f * LAM) * rho;
-  r = {LAM * drho, r3 * ux, r3 * uy, r3 * uz};
-  return make_float4(r.dr, r.vx, r.vy, r.vz);
+  const __half2 a = __floats2half2_rn(LAM * drho, r3 * ux), b = __floats2half2_rn(r3 * uy, r3 * uz);
+  const float2 fa = __half22float2(a), fb = __half22float2(b);
+  r = {fa.x, fa.y, fb.x, fb.y};
+  uint2 v;
+  v.x = *reinterpret_cast<const unsigned*>(&a);
+  v.y = *reinterpret_cast<const unsigned*>(&b);
+  return v;
 }
 
 // First-order equilibrium deviation of direction q about the reference,
@@ -115,9 +124,9 @@ __device__ __forceinline__ void store_sr(Dst&& dst_q, const float (&d)[Q], const
 }
 
 struct RefArgs {
-  const float4* refq[Q];  // refq[q][i]: reference of the upwind neighbour of node i
-  const float4* ref_src;  // references of the source step
-  float4* ref_dst;        // references written by this step
+  const uint2* refq[Q];  // refq[q][i]: reference of the upwind neighbour of node i
+  const uint2* ref_src;  // references of the source step
+  uint2* ref_dst;        // references written by this step
   unsigned step;         // the lattice's steps done before this one
 };
 
@@ -126,7 +135,7 @@ struct RefArgs {
 // reference of the node that wrote it: the upwind (or wrapped) node for a
 // streamed value, the node itself for a bounced one.
 __device__ __forceinline__ void pull_face_ref(const __half* __restrict__ src,
-                                              const float4* __restrict__ ref, int64_t qstride,
+                                              const uint2* __restrict__ ref, int64_t qstride,
                                               int nx, int ny, int nz, int pitch, int plane,
                                               unsigned fb, int x, int y, int z, int i,
                                               const float* lidc, float (&d)[Q]) {
@@ -188,7 +197,7 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         const __half* pq = a.srcq[q] + i;
-        const float4* rq = r.refq[q] + i;
+        const uint2* rq = r.refq[q] + i;
         float sgn = 1.0f, extra = 0.0f;
         if ((cx(q) == 1 && fl) || (cx(q) == -1 && fr)) {
           const int k = cx(q) == 1 ? kl : kr;
@@ -242,7 +251,7 @@ __global__ void __launch_bounds__(256, CAP ? 4 : 1) step_ref_kernel(const StepAr
 
 template <bool FORCE>
 __global__ void __launch_bounds__(256) fields_ref_kernel(const __half* __restrict__ src,
-                                                         const float4* __restrict__ ref, Geom g,
+                                                         const uint2* __restrict__ ref, Geom g,
                                                          CollideConst<float> C,
                                                          const float* __restrict__ lidc,
                                                          double* rho, double* u, double* gd) {
@@ -267,7 +276,7 @@ __global__ void __launch_bounds__(256) fields_ref_kernel(const __half* __restric
   if (gd) gd[k] = double(o.gamma_dot);
 }
 
-__global__ void export_ref_kernel(const __half* __restrict__ src, const float4* __restrict__ ref,
+__global__ void export_ref_kernel(const __half* __restrict__ src, const uint2* __restrict__ ref,
                                   Geom g, float rho0, double* __restrict__ out) {
   const int64_t N = int64_t(g.nx) * g.ny * g.nz;
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -283,7 +292,7 @@ __global__ void export_ref_kernel(const __half* __restrict__ src, const float4* 
 // One thread per node: the reference is the node's own moments of the
 // imported populations.
 __global__ void import_ref_kernel(const double* __restrict__ in, Geom g, float rho0,
-                                  __half* __restrict__ dst, float4* __restrict__ ref) {
+                                  __half* __restrict__ dst, uint2* __restrict__ ref) {
   const int64_t N = int64_t(g.nx) * g.ny * g.nz;
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= N) return;
@@ -367,8 +376,8 @@ __device__ void batch_node_ref(const LatDesc<float>& L, int parity, int x, int y
                                unsigned step, NodeOut<float>& o) {
   const __half* src = static_cast<const __half*>(L.buf[parity]);
   __half* dst = static_cast<__half*>(const_cast<void*>(L.buf[parity ^ 1]));
-  const float4* rs = static_cast<const float4*>(L.ref[parity]);
-  float4* rd = static_cast<float4*>(const_cast<void*>(L.ref[parity ^ 1]));
+  const uint2* rs = static_cast<const uint2*>(L.ref[parity]);
+  uint2* rd = static_cast<uint2*>(const_cast<void*>(L.ref[parity ^ 1]));
   const float rho0 = L.C.rho0;
   const int qs = int(L.qstride), plane = L.plane, pitch = L.pitch;
   const int i = z * plane + y * pitch + x;
@@ -417,18 +426,18 @@ cudaError_t launch_step_f16r(const void* src, void* dst, const void* ref_src, vo
   r.step = unsigned(uint64_t(step));
   const __half* s = static_cast<const __half*>(src);
   __half* d = static_cast<__half*>(dst);
-  const float4* rs = static_cast<const float4*>(ref_src);
+  const uint2* rs = static_cast<const uint2*>(ref_src);
   for (int q = 0; q < Q; ++q) {
     const int64_t off = int64_t(cz(q)) * g.plane + int64_t(cy(q)) * g.pitch + cx(q);
     a.srcq[q] = reinterpret_cast<const __half*>(reinterpret_cast<uintptr_t>(s) +
                                                  (int64_t(q) * g.qstride - off) * 2);
     a.dstq[q] = d + int64_t(q) * g.qstride;
-    r.refq[q] = reinterpret_cast<const float4*>(reinterpret_cast<uintptr_t>(rs) -
-                                                 off * int64_t(sizeof(float4)));
+    r.refq[q] = reinterpret_cast<const uint2*>(reinterpret_cast<uintptr_t>(rs) -
+                                                 off * int64_t(sizeof(uint2)));
   }
   lid_table(g, a.lidc);
   r.ref_src = rs;
-  r.ref_dst = static_cast<float4*>(ref_dst);
+  r.ref_dst = static_cast<uint2*>(ref_dst);
   a.zrev = reinterpret_cast<uintptr_t>(dst) < reinterpret_cast<uintptr_t>(src) ? 1 : 0;
   a.src = s;
   a.qstride = g.qstride;
@@ -473,7 +482,7 @@ cudaError_t launch_fields_f16r(const void* src, const void* ref, const Geom& g,
     dim3 grid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz);
     const CollideConst<float> C = make_const<float>(P, double(LAM));
     const __half* s = static_cast<const __half*>(src);
-    const float4* r = static_cast<const float4*>(ref);
+    const uint2* r = static_cast<const uint2*>(ref);
     if (P.has_force) fields_ref_kernel<true><<<grid, block, 0, st>>>(s, r, g, C, dlid, rho, u, gd);
     else fields_ref_kernel<false><<<grid, block, 0, st>>>(s, r, g, C, dlid, rho, u, gd);
     e = cudaGetLastError();
@@ -487,7 +496,7 @@ cudaError_t launch_export_f16r(const void* src, const void* ref, const Geom& g, 
   const int64_t total = int64_t(g.nx) * g.ny * g.nz * Q;
   const int b = 256;
   export_ref_kernel<<<unsigned((total + b - 1) / b), b, 0, st>>>(
-      static_cast<const __half*>(src), static_cast<const float4*>(ref), g, float(rho0), out);
+      static_cast<const __half*>(src), static_cast<const uint2*>(ref), g, float(rho0), out);
   return cudaGetLastError();
 }
 
@@ -497,7 +506,7 @@ cudaError_t launch_import_f16r(const double* in, const Geom& g, double rho0, voi
   const int b = 128;
   import_ref_kernel<<<unsigned((N + b - 1) / b), b, 0, st>>>(in, g, float(rho0),
                                                               static_cast<__half*>(dst),
-                                                              static_cast<float4*>(ref));
+                                                              static_cast<uint2*>(ref));
   return cudaGetLastError();
 }
 
