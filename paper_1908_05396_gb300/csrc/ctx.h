@@ -8,6 +8,12 @@
 #include "../../include/clbm.h"
 #include "launch.h"
 
+namespace clbm {
+// Bytes of the F16R form's reference arrays (four FP16 values per stored node, and
+// slack for the stencil's reach past the last node), per buffer.
+inline size_t f16r_ref_bytes(int64_t stored_nodes) { return size_t(stored_nodes + 64) * 8; }
+}  // namespace clbm
+
 struct clbm_ctx {
   int device = 0;
   clbm_domain dom{};

@@ -13,10 +13,6 @@ enum { DT_F64 = 0, DT_F32 = 1, DT_F16S = 2, DT_F16R = 3 };
 // Power-of-two scale of the FP16 shifted storage: stored = (f - w rho0) * 1024.
 constexpr double F16_SCALE = 1024.0;
 
-// Bytes of the F16R form's reference arrays (four FP16 values per stored node, and
-// slack for the stencil's reach past the last node), per buffer.
-inline size_t f16r_ref_bytes(int64_t stored_nodes) { return size_t(stored_nodes + 64) * 8; }
-
 // Lattice geometry and the stored layout pop[q][z][y][x] with row pitch.
 struct Geom {
   int nx, ny, nz;
