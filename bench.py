@@ -279,7 +279,18 @@ def run_reference(args):
     return 0
 
 
-def _time_form(clbm, torch, dtype, steps, warmup, stream, in_place=False):
+def form_spec(name: str):
+    """(dtype, in_place, rounding) of a form name: a storage form, optionally
+    with "_inplace" (one buffer streamed in place) or "_sr" (F16S with
+    stochastically rounded stores)."""
+    if name.endswith("_inplace"):
+        return name[:-len("_inplace")], True, None
+    if name.endswith("_sr"):
+        return name[:-len("_sr")], False, "stochastic"
+    return name, False, None
+
+
+def _time_form(clbm, torch, dtype, steps, warmup, stream, in_place=False, rounding=None):
     """MLUPS of one storage form over the three cavities, each lattice stepping
     on its own stream so that one lattice's launch gaps and tail waves are
     filled by the others' work; the timed region is fenced by events on
@@ -288,6 +299,9 @@ def _time_form(clbm, torch, dtype, steps, warmup, stream, in_place=False):
     streams = [torch.cuda.Stream() for _ in NS_BENCH]
     lats = [clbm.Lattice(**wl.cavity(L_BENCH, RE_BENCH, n).kwargs(), dtype=dtype,
                          stream=s.cuda_stream, in_place=in_place) for n, s in zip(NS_BENCH, streams)]
+    if rounding:
+        for lt in lats:
+            lt.set_rounding(rounding)
     tuned = [lt.autotune(10) for lt in lats]     # launch shape per lattice (cached)
     N = lats[0].N
     for _ in range(warmup):
@@ -359,14 +373,14 @@ def run_ours(args):
     # ---- the other forms ------------------------------------------------------
     forms = {}
     form_steps = {"f64": max(3, args.steps // 40), "f16s": args.steps, "f16r": args.steps}
-    form_steps["f32_inplace"] = args.steps
-    for name in ("f64", "f16s", "f16r", "f32_inplace"):
+    form_steps["f32_inplace"] = form_steps["f16s_sr"] = args.steps
+    for name in ("f64", "f16s", "f16s_sr", "f16r", "f32_inplace"):
         if args.forms and name not in args.forms:
             continue
-        dt, ip = (name[:-len("_inplace")], True) if name.endswith("_inplace") else (name, False)
+        dt, ip, rnd = form_spec(name)
         barrier()
         ms_f, N_f, launches_f, tuned_f = _time_form(clbm, torch, dt, form_steps[name], args.warmup,
-                                                    stream, in_place=ip)
+                                                    stream, in_place=ip, rounding=rnd)
         mlups = N_f * len(NS_BENCH) * form_steps[name] / (ms_f * 1e-3) / 1e6
         gbs = BYTES_PER_UPDATE[dt] * N_f * launches_f / (ms_f * 1e-3) / 1e9
         forms[name] = {"MLUPS": mlups, "GB/s": gbs, "frac_of_hbm": gbs / peak,
@@ -374,6 +388,8 @@ def run_ours(args):
                        "launch": [(t["block"], t["npt"]) for t in tuned_f]}
         if ip:
             forms[name]["what"] = "one population buffer streamed in place (half the memory)"
+        if rnd:
+            forms[name]["what"] = "F16S storage with stochastically rounded stores"
     forms[head] = {"MLUPS": value / ws, "GB/s": achieved, "frac_of_hbm": achieved / peak,
                    "steps": args.steps, "bytes_per_update": bpn,
                    "launch": [(t["block"], t["npt"]) for t in tuned]}
@@ -697,7 +713,10 @@ def _run_to_steady(clbm, prob, dtype, tol, max_steps, plateau=20, chunk=1000, ch
     (populations, steps) continues from a stored state; `snapshot_at` keeps
     the populations after that many steps (returned in the info)."""
     snap = None
-    with clbm.Lattice(**prob.kwargs(), dtype=dtype, check_interval=check) as lat:
+    dt_, ip_, rnd_ = form_spec(dtype)
+    with clbm.Lattice(**prob.kwargs(), dtype=dt_, in_place=ip_, check_interval=check) as lat:
+        if rnd_:
+            lat.set_rounding(rnd_)
         lat.autotune(5)
         best, since, steps, R, status = float("inf"), 0, 0, float("inf"), "max_steps"
         if start is not None:
@@ -747,18 +766,22 @@ def run_precision(args):
     out = {"metric": "precision", "cases": []}
     prob = wl.cavity(64, 100.0, 0.8)
     res = {}
-    for dt in ("f64", "f32", "f16s", "f16r"):
+    forms = ("f64", "f32", "f16s", "f16s_sr", "f16r")
+    for dt in forms:
         res[dt] = _run_to_steady(clbm, prob, dt, 1e-8, 600_000)
     n64 = float(np.linalg.norm(res["f64"][0]))
     out["cases"].append({
         "case": "cavity 64^3, Re 100, n 0.8, U 0.05, run to R <= 1e-8 (F16S: or plateau)",
         "runs": {k: v[1] for k, v in res.items()},
         "l2_vs_f64": {k: float(np.linalg.norm(res[k][0] - res["f64"][0])) / n64
-                      for k in ("f32", "f16s", "f16r")}})
+                      for k in forms[1:]}})
     prob = wl.cavity(256, 1000.0, 0.8)
     fixed = {}
-    for dt in ("f64", "f32", "f16s", "f16r"):
-        with clbm.Lattice(**prob.kwargs(), dtype=dt) as lat:
+    for dt in forms:
+        dt_, ip_, rnd_ = form_spec(dt)
+        with clbm.Lattice(**prob.kwargs(), dtype=dt_, in_place=ip_) as lat:
+            if rnd_:
+                lat.set_rounding(rnd_)
             lat.autotune(3)
             t0 = time.perf_counter()
             lat.step(args.precision_steps)
@@ -771,7 +794,7 @@ def run_precision(args):
         "case": f"cavity 256^3, Re 1000, n 0.8, U 0.05, {args.precision_steps} steps from rest",
         "seconds": {k: v[1] for k, v in fixed.items()},
         "l2_vs_f64": {k: float(np.linalg.norm(fixed[k][0] - fixed["f64"][0])) / n64
-                      for k in ("f32", "f16s", "f16r")}})
+                      for k in forms[1:]}})
     print(json.dumps(out))
     return 0
 
@@ -967,8 +990,8 @@ def main():
     ap.add_argument("--precision-f64-from", type=int, default=0,
                     help="--precision-steady: start FP64 from the FP32 state after this many "
                          "steps (0: from rest)")
-    ap.add_argument("--precision-forms", nargs="*", default=["f64", "f32", "f16r", "f16s"],
-                    choices=["f64", "f32", "f16r", "f16s"],
+    ap.add_argument("--precision-forms", nargs="*", default=["f64", "f32", "f16r", "f16s", "f16s_sr"],
+                    choices=["f64", "f32", "f16r", "f16s", "f16s_sr"],
                     help="forms of --precision-steady, the first the reference unless FP64 runs")
     ap.add_argument("--profile-batch", action="store_true",
                     help="time only the batch of 64 cavities (profiling case)")

@@ -57,8 +57,8 @@ extern "C" {
 /* Storage precision of the populations.
  *   CLBM_F64  : f - w rho0 stored in FP64, collision in FP64.
  *   CLBM_F32  : f - w rho0 stored in FP32, collision in FP32.
- *   CLBM_F16S : (f - w rho0) * 1024 stored in FP16 (round to nearest even),
- *               collision in FP32.
+ *   CLBM_F16S : (f - w rho0) * 1024 stored in FP16 (round to nearest even,
+ *               or stochastic rounding: clbm_set_rounding), collision in FP32.
  *   CLBM_F16R : (f - w [rho0 + drho + 3 (rho0 + drho)(e . u)]) * 1024 in
  *               FP16 with stochastic rounding, relative to the writing node's
  *               own (drho, 3 (rho0 + drho) u), which is stored beside the
@@ -216,6 +216,26 @@ int clbm_set_launch(clbm_handle h, int block_x, int block_y, int npt);
  * omega_nu.  Takes effect from the next step.  Not for a lattice in a batch
  * (CLBM_ERR_ARG: detach it first).  Errors: CLBM_ERR_ARG. */
 int clbm_set_rates(clbm_handle h, const double omega[10]);
+
+/* Rounding of the FP16 stores of an F16S lattice (not in the paper, which
+ * computes in one precision).  CLBM_ROUND_NEAREST (the default) rounds each
+ * stored value to the nearest FP16 value.  Near a steady state the per-step
+ * change of a stored value falls below half an FP16 ulp and is rounded away,
+ * so the state freezes short of the steady state.  CLBM_ROUND_STOCHASTIC
+ * rounds up in magnitude with probability equal to the fraction of an ulp the
+ * value carries, from random bits that depend only on the node and the
+ * lattice's step count (the same bits alone and in any run); such changes
+ * then survive on average.  The stored layout does not change.  Stochastic
+ * rounding runs the one-node-per-thread step kernel only (npt 1 or 5);
+ * clbm_set_rounding resets another launch shape to npt 1, and a batch does
+ * not take such a lattice (clbm_batch_add: CLBM_ERR_UNSUPPORTED).  Errors:
+ * CLBM_ERR_UNSUPPORTED for other storage forms (F16R always rounds
+ * stochastically and accepts CLBM_ROUND_STOCHASTIC as a no-op; FP32 and FP64
+ * accept CLBM_ROUND_NEAREST as a no-op) and for stochastic rounding of an
+ * in-place lattice; CLBM_ERR_ARG for an invalid handle, an unknown mode or a
+ * lattice in a batch (detach it first). */
+typedef enum { CLBM_ROUND_NEAREST = 0, CLBM_ROUND_STOCHASTIC = 1 } clbm_rounding;
+int clbm_set_rounding(clbm_handle h, clbm_rounding mode);
 
 /* ---- Batched stepping of many lattices --------------------------------
  * Not in the paper: a batch steps up to `capacity` lattices of one storage

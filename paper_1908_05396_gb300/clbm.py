@@ -17,6 +17,7 @@ from . import build as _build
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DIVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 F64, F32, F16S, F16R = 0, 1, 2, 3
 PERIODIC, WALL, LID = 0, 1, 2
+ROUND_NEAREST, ROUND_STOCHASTIC = 0, 1
 DTYPES = {"f64": F64, "f32": F32, "f16s": F16S, "f16r": F16R}
 
 _LOCK = threading.Lock()
@@ -83,12 +84,13 @@ def lib():
                                         _D]
             L.clbm_set_launch.argtypes = [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             L.clbm_set_rates.argtypes = [_H, _D]
+            L.clbm_set_rounding.argtypes = [_H, ctypes.c_int]
             L.clbm_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, ctypes.c_void_p]
             L.clbm_probe_fma_rate.argtypes = [ctypes.c_int, _D]
             L.clbm_omega_nodes.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_double, _D, _D, _D, _D,
                                            ctypes.c_int64]
-            for name in ("clbm_probe_fma_rate", "clbm_omega_nodes", "clbm_autotune", "clbm_set_launch", "clbm_set_rates", "clbm_set_allocator",
+            for name in ("clbm_probe_fma_rate", "clbm_omega_nodes", "clbm_autotune", "clbm_set_launch", "clbm_set_rates", "clbm_set_rounding", "clbm_set_allocator",
                          "clbm_create", "clbm_step", "clbm_fields", "clbm_fields_device",
                          "clbm_residual", "clbm_mass", "clbm_get_state", "clbm_set_state",
                          "clbm_steps_done", "clbm_sync", "clbm_destroy", "clbm_collide_nodes"):
@@ -259,6 +261,13 @@ class Lattice:
         w = np.ascontiguousarray(omega, dtype=np.float64)
         assert w.shape == (10,)
         _check(lib().clbm_set_rates(self._h, _dp(w)), self._h)
+
+    def set_rounding(self, mode) -> None:
+        """FP16 store rounding of an F16S lattice: ROUND_NEAREST (default) or
+        ROUND_STOCHASTIC (also accepted as "nearest" / "stochastic")."""
+        if isinstance(mode, str):
+            mode = {"nearest": ROUND_NEAREST, "stochastic": ROUND_STOCHASTIC}[mode]
+        _check(lib().clbm_set_rounding(self._h, int(mode)), self._h)
 
     def set_launch(self, block_x: int, block_y: int, npt: int) -> None:
         _check(lib().clbm_set_launch(self._h, int(block_x), int(block_y), int(npt)), self._h)

@@ -551,6 +551,9 @@ int clbm_batch_add(clbm_batch b, clbm_handle h, int* slot) {
                  "in-place lattices join a batch only in its one-launch-per-lattice mode "
                  "(clbm_batch_set_lattice_launch): the persistent kernel's tiles need two buffers");
   if (h->device != b->device) return bfail(b, CLBM_ERR_ARG, "lattice lives on another device");
+  if (h->sround)
+    return bfail(b, CLBM_ERR_UNSUPPORTED,
+                 "batches step F16S lattices with round-to-nearest stores only");
   if (h->batch) return bfail(b, CLBM_ERR_ARG, "lattice is already in a batch");
   if (int64_t(NQ) * h->g.qstride >= (int64_t(1) << 31))
     return bfail(b, CLBM_ERR_UNSUPPORTED, "lattice too large to batch (19 x padded nodes >= 2^31)");

@@ -21,6 +21,7 @@
 #include "ctx.h"
 #include "launch.h"
 #include "validate.h"
+#include "launch_f16sr.h"
 
 using namespace clbm;
 
@@ -101,7 +102,11 @@ cudaError_t dispatch_step(clbm_ctx* h, bool check) {
     case CLBM_F16R:
       return launch_step_f16r(src, dst, h->ref[h->cur], h->ref[1 - h->cur], h->g, h->P, cb, check,
                               h->block, h->npt, h->steps, h->stream);
-    default: return launch_step_f16(src, dst, h->g, h->P, cb, check, h->block, h->npt, h->stream);
+    default:
+      if (h->sround)
+        return launch_step_f16sr(src, dst, h->g, h->P, cb, check, h->block, h->npt, h->steps,
+                                 h->stream);
+      return launch_step_f16(src, dst, h->g, h->P, cb, check, h->block, h->npt, h->stream);
   }
 }
 
@@ -454,7 +459,7 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
   if (bad(h)) return fail(h, CLBM_ERR_ARG, "invalid handle");
   if (int r = set_device(h)) return r;
   if (steps <= 0) steps = 10;
-  const auto key = std::make_tuple(int(h->dtype) + (h->in_place ? 16 : 0), h->g.nx, h->g.ny,
+  const auto key = std::make_tuple(int(h->dtype) + (h->in_place ? 16 : 0) + (h->sround ? 32 : 0), h->g.nx, h->g.ny,
                                    h->g.nz, h->P.has_force, h->P.newtonian);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -476,7 +481,7 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
   const int shapes[][2] = {{32, 1}, {32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2}, {64, 4},
                            {128, 1}, {128, 2}, {256, 1}};
   for (int capped = 0; capped <= 1; ++capped)
-    for (int np = 1; np <= ((h->dtype == CLBM_F64 || h->dtype == CLBM_F16R || h->in_place) ? 1 : 2); ++np)
+    for (int np = 1; np <= ((h->dtype == CLBM_F64 || h->dtype == CLBM_F16R || h->in_place || h->sround) ? 1 : 2); ++np)
       for (auto& sh : shapes) {
         if (sh[0] * sh[1] > (np == 2 ? 128 : 256)) continue;
         if (sh[0] > 32 && sh[0] > h->g.pitch) continue;
@@ -488,7 +493,7 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
     for (int capped = 0; capped <= 1; ++capped)
       for (int t : {64, 128, 256}) cands.push_back({tw, t / tw, 1 + 4 * capped});
   // FP32 and FP16 storage: the TMA-staged kernel in each of its shapes
-  if ((h->dtype == CLBM_F32 || h->dtype == CLBM_F16S) && !h->in_place)
+  if ((h->dtype == CLBM_F32 || h->dtype == CLBM_F16S) && !h->in_place && !h->sround)
     for (int v = 0; v < TMA_NVAR; ++v) cands.push_back({tma_bx(v), tma_by(v), TMA_NPT + 32 * v});
   // Save the state: tuning runs real steps.
   const size_t pop_bytes = size_t(NQ) * size_t(h->g.qstride) * h->elem;
@@ -562,6 +567,28 @@ int clbm_autotune(clbm_handle h, int steps, int* block_x, int* block_y, int* npt
   return CLBM_OK;
 }
 
+int clbm_set_rounding(clbm_handle h, clbm_rounding mode) {
+  if (bad(h)) return fail(h, CLBM_ERR_ARG, "invalid handle");
+  if (mode != CLBM_ROUND_NEAREST && mode != CLBM_ROUND_STOCHASTIC)
+    return fail(h, CLBM_ERR_ARG, "unknown rounding mode");
+  if (h->batch) return fail(h, CLBM_ERR_ARG, "lattice is in a batch: detach it first");
+  const bool sr = mode == CLBM_ROUND_STOCHASTIC;
+  if (h->dtype == CLBM_F16R) {
+    if (!sr) return fail(h, CLBM_ERR_UNSUPPORTED, "the F16R form always rounds stochastically");
+    return CLBM_OK;
+  }
+  if (h->dtype != CLBM_F16S) {
+    if (sr) return fail(h, CLBM_ERR_UNSUPPORTED, "stochastic rounding is an F16S option");
+    return CLBM_OK;
+  }
+  if (sr && h->in_place)
+    return fail(h, CLBM_ERR_UNSUPPORTED, "stochastic rounding takes two-buffer lattices");
+  h->sround = sr;
+  // the stochastic kernel has one shape family: one node per thread
+  if (sr && ((h->npt & TMA_NPT) || (h->npt & 3) == 2)) h->npt = 1;
+  return CLBM_OK;
+}
+
 int clbm_set_rates(clbm_handle h, const double omega[10]) {
   if (bad(h) || !omega) return fail(h, CLBM_ERR_ARG, "invalid handle or rates");
   if (h->batch) return fail(h, CLBM_ERR_ARG, "lattice is in a batch: detach it first");
@@ -582,6 +609,8 @@ int clbm_set_launch(clbm_handle h, int block_x, int block_y, int npt) {
       return fail(h, CLBM_ERR_ARG, "npt: TMA_NPT + 32 v with v < TMA_NVAR for the TMA kernel");
     if (h->dtype != CLBM_F32 && h->dtype != CLBM_F16S)
       return fail(h, CLBM_ERR_UNSUPPORTED, "the TMA-staged kernel takes FP32 or F16S storage");
+    if (h->sround)
+      return fail(h, CLBM_ERR_UNSUPPORTED, "stochastic rounding runs one node per thread (npt 1 or 5)");
     if (block_x != tma_bx(v) || block_y != tma_by(v))
       return fail(h, CLBM_ERR_ARG, "block does not match the TMA shape");
     h->block = dim3(block_x, block_y, 1);
@@ -597,6 +626,8 @@ int clbm_set_launch(clbm_handle h, int block_x, int block_y, int npt) {
                                  "(128 with two nodes per thread)");
   if (np == 2 && (h->dtype == CLBM_F64 || h->dtype == CLBM_F16R))
     return fail(h, CLBM_ERR_UNSUPPORTED, "two nodes per thread needs FP32 math");
+  if (np == 2 && h->sround)
+    return fail(h, CLBM_ERR_UNSUPPORTED, "stochastic rounding runs one node per thread (npt 1 or 5)");
   h->block = dim3(block_x, block_y, 1);
   h->npt = npt;
   return CLBM_OK;

@@ -26,6 +26,7 @@ struct clbm_ctx {
   void* ref[2] = {nullptr, nullptr};  // F16R: per-node reference moments, with buf
   int cur = 0;           // buffer holding the current state (0 when in place)
   bool in_place = false; // one buffer, streamed in place (inplace.cuh)
+  bool sround = false;   // F16S: stores rounded stochastically (step_f16sr.cu)
   int layout = 0;        // in place: the layout the buffer holds (0 swapped, 1 streamed)
   void* uprev = nullptr;
   double* acc = nullptr; // device: 3 doubles, then the int flag and the TMA error word

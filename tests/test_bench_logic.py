@@ -36,3 +36,10 @@ def test_profile_notes_match_only_current_sources(tmp_path, monkeypatch):
     assert bench._traffic_note("step_kernel<float>") == 276000000.0
     assert bench._traffic_note("step_kernel<half>") is None
     assert bench._fp64_ops_note("step_kernel<double>") == [1.5, 2.5, 3.0]
+
+
+def test_form_names():
+    import bench
+    assert bench.form_spec("f16s_sr") == ("f16s", False, "stochastic")
+    assert bench.form_spec("f32_inplace") == ("f32", True, None)
+    assert bench.form_spec("f16r") == ("f16r", False, None)
