@@ -584,7 +584,10 @@ def _batch_bench(clbm, torch, wl, steps, peak):
 def _serve_trace(clbm, trace, dtype, tol, cap, plateau, check):
     """Replay the trace through the continuous-batching server (requests
     submitted at their arrival times); every request keeps its fields."""
-    with clbm.Server(dtype, hbm_budget_bytes=150e9, max_active=64, check_interval=check) as srv:
+    dt_, _, rnd_ = form_spec(dtype)
+    with clbm.Server(dt_, hbm_budget_bytes=150e9, max_active=64, check_interval=check) as srv:
+        if rnd_:
+            srv.set_rounding(rnd_)
         t0 = time.perf_counter()
         ids = []
         for r in trace:
@@ -640,15 +643,16 @@ def _solve_alone(clbm, prob, dtype, tol, cap, plateau, check):
 
 
 def _serving_bench(clbm, trace, tol, cap, plateau, check, workload, bars=None):
-    """The trace through the continuous-batching server in three storage
-    forms (F16R, the headline, F16S and FP32), and the same requests solved
+    """The trace through the continuous-batching server in four storage
+    forms (F16R, the headline; F16S with stochastic and with round-to-nearest
+    stores; FP32), and the same requests solved
     one at a time by plain single-instance FP64 handles with the same
     stopping rule and check interval (the solves/s baseline).  Each served
     result is compared with the FP64 result of the same request: at the same
     step count where both stopped on the step cap, else at each one's own end
     (its steady state when both converged)."""
     import numpy as np
-    bars = bars or {"f16r": 2e-3, "f16s": 2e-3, "f32": 1e-4}
+    bars = bars or {"f16r": 2e-3, "f16s": 2e-3, "f16s_sr": 2e-3, "f32": 1e-4}
     t0 = time.perf_counter()
     base = [_solve_alone(clbm, r.problem, "f64", tol, cap, plateau, check) for r in trace]
     seq_dt = time.perf_counter() - t0
@@ -656,7 +660,7 @@ def _serving_bench(clbm, trace, tol, cap, plateau, check, workload, bars=None):
     for st, _, _ in base:
         base_status[st] = base_status.get(st, 0) + 1
     forms = {}
-    for dt in ("f16r", "f16s", "f32"):
+    for dt in ("f16r", "f16s_sr", "f16s", "f32"):
         res, fields, info = _serve_trace(clbm, trace, dt, tol, cap, plateau, check)
         out = _latency_stats(clbm, res)
         out["server_MLUPS"] = info["lattice_updates"] / max(info["busy_seconds"], 1e-9) / 1e6
@@ -675,7 +679,7 @@ def _serving_bench(clbm, trace, tol, cap, plateau, check, workload, bars=None):
     head.update({
         "form": "f16r", "workload": workload,
         "rule": f"tol {tol}, step cap {cap}, plateau {plateau} checks, check interval {check} steps",
-        "other_forms": {dt: forms[dt] for dt in ("f16s", "f32")},
+        "other_forms": {dt: forms[dt] for dt in ("f16s_sr", "f16s", "f32")},
         "sequential_f64": {"solves_per_s": len(trace) / seq_dt, "seconds": seq_dt,
                            "status": base_status,
                            "what": "the same requests one at a time, plain FP64 handles, same rule"},
@@ -701,7 +705,7 @@ def run_serve_steady(args):
     wk = (f"{len(trace)} requests, Poisson 20/s (seed 0), half cavities L~U{{16..48}}, half "
           "channels 8xU{16..64}x8, Re~U[50,400], n~U[0.4,1.6]")
     out = _serving_bench(clbm, trace, 1e-7, 400_000, 20, 4000, wk,
-                         bars={"f16r": 2e-3, "f16s": 2e-3, "f32": 1e-4})
+                         bars={"f16r": 2e-3, "f16s": 2e-3, "f16s_sr": 2e-3, "f32": 1e-4})
     print(json.dumps({"metric": "served solves/s, p50/p99, to steady state", "serving": out}))
     return 0
 

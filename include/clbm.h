@@ -360,6 +360,10 @@ typedef struct clbm_server_ctx* clbm_server;
 /* The server's lattices live on the device current at creation. */
 int clbm_server_create(clbm_dtype dtype, double hbm_budget_bytes, int max_active,
                        int check_interval, clbm_server* out);
+/* Store rounding of the lattices an F16S server admits from now on
+ * (clbm_set_rounding; default CLBM_ROUND_NEAREST).  The same errors as
+ * clbm_set_rounding for the server's storage form. */
+int clbm_server_set_rounding(clbm_server s, clbm_rounding mode);
 /* Queue a request (thread-safe); *id identifies it. */
 int clbm_server_submit(clbm_server s, const clbm_request* req, int64_t* id);
 /* Block until request id is finished (timeout_s < 0: no limit); returns

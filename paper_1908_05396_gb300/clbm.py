@@ -545,12 +545,13 @@ class Server:
             L.clbm_server_fields.argtypes = [S, ctypes.c_int64, _D, _D, _D]
             L.clbm_server_release.argtypes = [S, ctypes.c_int64]
             L.clbm_server_info.argtypes = [S, ctypes.POINTER(ServerStats)]
+            L.clbm_server_set_rounding.argtypes = [S, ctypes.c_int]
             L.clbm_server_destroy.argtypes = [S]
             L.clbm_server_last_error.argtypes = [S]
             L.clbm_server_last_error.restype = ctypes.c_char_p
             for n in ("clbm_server_create", "clbm_server_submit", "clbm_server_wait",
                       "clbm_server_results", "clbm_server_fields", "clbm_server_release",
-                      "clbm_server_info", "clbm_server_destroy"):
+                      "clbm_server_info", "clbm_server_set_rounding", "clbm_server_destroy"):
                 getattr(L, n).restype = ctypes.c_int
             L._server_ready = True
         self._s = ctypes.c_void_p()
@@ -566,6 +567,13 @@ class Server:
         if rc != OK:
             msg = lib().clbm_server_last_error(self._s)
             raise CLBMError(rc, msg.decode() if msg else "")
+
+    def set_rounding(self, mode) -> None:
+        """Store rounding of the lattices admitted from now on (F16S servers):
+        ROUND_NEAREST or ROUND_STOCHASTIC, or "nearest" / "stochastic"."""
+        if isinstance(mode, str):
+            mode = {"nearest": ROUND_NEAREST, "stochastic": ROUND_STOCHASTIC}[mode]
+        self._scheck(lib().clbm_server_set_rounding(self._s, int(mode)))
 
     def submit(self, nx, ny, nz, face, K, n, U_lid=None, body_force=None, tol=1e-7,
                max_steps=0, plateau_checks=0, keep_fields=False, rho0=1.0, nu_min=0.0,

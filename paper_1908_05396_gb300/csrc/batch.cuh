@@ -12,6 +12,7 @@
 #pragma once
 
 #include "kernels.cuh"
+#include "sround.cuh"
 
 namespace clbm {
 
@@ -26,7 +27,8 @@ struct LatDesc {
   int tiles_x, tiles_y;
   int tw_log2;         // tile width (nodes along x) = 1 << tw_log2, height = threads / width
   int slot;            // row of this lattice in the batch's reduction array
-  unsigned step_offset;  // F16R: lattice steps minus batch steps (seeds its rounding)
+  unsigned step_offset;  // lattice steps minus batch steps (seeds stochastic rounding)
+  int sround;            // F16S: stores rounded stochastically
   R lidc[Q];
   CollideConst<R> C;
 };
@@ -38,7 +40,7 @@ struct LatDesc {
 template <typename S, typename R, bool FORCE>
 __device__ __forceinline__ void batch_node(const LatDesc<R>& L, const S* __restrict__ src,
                                            S* __restrict__ dst, int x, int y, int z,
-                                           NodeOut<R>& o) {
+                                           unsigned step, NodeOut<R>& o) {
   const int qs = int(L.qstride), plane = L.plane, pitch = L.pitch;
   const int i = z * plane + y * pitch + x;
   R d[Q];
@@ -70,6 +72,19 @@ __device__ __forceinline__ void batch_node(const LatDesc<R>& L, const S* __restr
                     L.lidc, d);
   }
   collide<R, FORCE, pair_out<S>(), log2_scale<S>()>(L.C, d, o);
+  if constexpr (std::is_same<S, __half>::value) {
+    if (L.sround) {  // as step_f16sr.cu: two directions per stochastic conversion
+      uint32_t state = sr_seed(uint32_t(i), step);
+#pragma unroll
+      for (int q = 0; q < Q; q += 2) {
+        __half hi, lo;
+        enc16_sr2(d[q], q + 1 < Q ? d[q + 1 < Q ? q + 1 : q] : 0.0f, state, hi, lo);
+        dst[q * qs + i] = hi;
+        if (q + 1 < Q) dst[(q + 1 < Q ? q + 1 : q) * qs + i] = lo;
+      }
+      return;
+    }
+  }
 #pragma unroll
   for (int q = 0; q < Q; ++q) dst[q * qs + i] = Codec<S, R>::enc(d[q], R(1));
 }
@@ -93,10 +108,12 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
                                             const unsigned* __restrict__ coord,
                                             BatchHeader* hdr, int parity, double* acc, int zc) {
   // tiles [0, ntiles0) belong to lattices without force, [ntiles0, ntiles) with
-  // F16R: this chain's step count, advanced at the end of each of its
-  // launches by the launch's last CTA
+  // F16R and F16S (whose lattices may round stochastically): this chain's
+  // step count, advanced at the end of each of its launches by the launch's
+  // last CTA
+  constexpr bool STEPS = REF || std::is_same<S, __half>::value;
   const unsigned bstep =
-      REF ? *reinterpret_cast<volatile const unsigned*>(&hdr->step[FORCE ? 1 : 0]) : 0u;
+      STEPS ? *reinterpret_cast<volatile const unsigned*>(&hdr->step[FORCE ? 1 : 0]) : 0u;
   const int t0 = FORCE ? hdr->ntiles0 : 0;
   const int t1 = FORCE ? hdr->ntiles : hdr->ntiles0;
   const int nlat = hdr->nlat;
@@ -145,7 +162,7 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
       if (active) {
         NodeOut<R> o;
         if constexpr (REF) batch_node_ref<FORCE>(L, parity, x, y, z, bstep + L.step_offset, o);
-        else batch_node<S, R, FORCE>(L, src, dst, x, y, z, o);
+        else batch_node<S, R, FORCE>(L, src, dst, x, y, z, bstep + L.step_offset, o);
         if (CHECK) {
           R* up = static_cast<R*>(L.uprev);
           const int64_t nst = int64_t(L.plane) * L.nz;
@@ -176,7 +193,7 @@ __device__ __forceinline__ void batch_tiles(Get get, const int* __restrict__ own
         atomicOr(reinterpret_cast<int*>(&a[3]), 1);
     }
   }
-  if constexpr (REF) {
+  if constexpr (STEPS) {
     // every CTA of this launch has read its chain's step count: the last one
     // to finish advances it
     __syncthreads();
@@ -218,6 +235,7 @@ void fill_desc_t(void* out, double lam, const Geom& g, const PhysParams& P, cons
   L.tw_log2 = tw_log2;
   L.slot = slot;
   L.step_offset = step_offset;
+  L.sround = 0;
   for (int q = 0; q < Q; ++q)
     L.lidc[q] = R(6.0 * wt<double>(q) * g.rho0 * lam *
                   (cx(q) * g.U[0] + cy(q) * g.U[1] + cz(q) * g.U[2]));
@@ -274,6 +292,9 @@ void fill_desc_t(void* out, double lam, const Geom& g, const PhysParams& P, cons
     /* the F16R form carries unscaled deviations; FP16-shifted ones are scaled */            \
     fill_desc_t<R>(out, double(1 << log2_scale<S>()), g, P, cur, other, ref_cur,             \
                    ref_other, uprev, tx, ty, twl, slot, so);                                   \
+  }                                                                                            \
+  void desc_set_sround_##SUFFIX(void* out, int on) {                                           \
+    static_cast<LatDesc<R>*>(out)->sround = on;                                                \
   }                                                                                            \
   cudaError_t upload_desc_##SUFFIX(const void* host, int base, int n) {                        \
     return cudaMemcpyToSymbol(c_lat_##SUFFIX, host, size_t(n) * sizeof(LatDesc<R>),            \

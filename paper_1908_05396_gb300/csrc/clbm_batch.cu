@@ -30,6 +30,7 @@
 #include "../../include/clbm.h"
 #include "ctx.h"
 #include "launch.h"
+#include "launch_f16sr.h"
 
 using namespace clbm;
 
@@ -157,8 +158,19 @@ void fill_desc(clbm_dtype t, void* out, const clbm_ctx* h, int tx, int ty, int t
     fill_desc_f32(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, twl, slot, so);
   else if (t == CLBM_F16R)
     fill_desc_f16r(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, twl, slot, so);
-  else
+  else {
     fill_desc_f16(out, h->g, h->P, cur, other, rcur, rother, h->uprev, tx, ty, twl, slot, so);
+    desc_set_sround_f16(out, h->sround ? 1 : 0);
+  }
+}
+
+// Whether an attached lattice rounds its stores stochastically: its seeds
+// come from the batch's device-side step count, which only the persistent
+// kernel advances (a replayed graph of per-lattice launches would repeat them).
+bool any_sround(const clbm_batch_ctx* b) {
+  for (int s = 0; s < b->capacity; ++s)
+    if (b->slots[s] && b->slots[s]->sround) return true;
+  return false;
 }
 
 // One step of the persistent kernel: the unforced lattices' launch on
@@ -551,9 +563,10 @@ int clbm_batch_add(clbm_batch b, clbm_handle h, int* slot) {
                  "in-place lattices join a batch only in its one-launch-per-lattice mode "
                  "(clbm_batch_set_lattice_launch): the persistent kernel's tiles need two buffers");
   if (h->device != b->device) return bfail(b, CLBM_ERR_ARG, "lattice lives on another device");
-  if (h->sround)
+  if (h->sround && b->mode == 1)
     return bfail(b, CLBM_ERR_UNSUPPORTED,
-                 "batches step F16S lattices with round-to-nearest stores only");
+                 "lattices with stochastic rounding take the persistent kernel, not the "
+                 "one-launch-per-lattice mode");
   if (h->batch) return bfail(b, CLBM_ERR_ARG, "lattice is already in a batch");
   if (int64_t(NQ) * h->g.qstride >= (int64_t(1) << 31))
     return bfail(b, CLBM_ERR_UNSUPPORTED, "lattice too large to batch (19 x padded nodes >= 2^31)");
@@ -667,6 +680,9 @@ int clbm_batch_set_lattice_launch(clbm_batch b, int block_x, int block_y, int np
   if (b->dtype == CLBM_F16R)
     return bfail(b, CLBM_ERR_UNSUPPORTED,
                  "F16R batches take the persistent kernel (its rounding is seeded by the step)");
+  if (any_sround(b))
+    return bfail(b, CLBM_ERR_UNSUPPORTED,
+                 "a lattice rounds stochastically: the batch takes the persistent kernel");
   if (block_x < 1 || block_y < 1 || block_x * block_y > 256 || (block_x * block_y) % 32 ||
       (npt != 1 && npt != 5) || streams < 1 || streams > 16)
     return bfail(b, CLBM_ERR_ARG, "bad launch shape");
@@ -763,9 +779,10 @@ int clbm_batch_autotune(clbm_batch b, int steps, int* block_x, int* block_y, int
           bc = capped != 0;
         }
       }
-  // One launch per lattice (not for F16R): block x kernel variant x streams.
+  // One launch per lattice (not for F16R, nor with a stochastically rounding
+  // lattice): block x kernel variant x streams.
   int bmode = 0, pbx = 32, pby = 2, pnpt = 5, pst = 4;
-  if (b->dtype != CLBM_F16R) {
+  if (b->dtype != CLBM_F16R && !any_sround(b)) {
     const int pshapes[][2] = {{32, 2}, {32, 4}, {64, 2}};
     const int pnpts[] = {5, 1};
     const int pstreams[] = {2, 4, 8};

@@ -59,6 +59,7 @@ struct Done {
 
 struct clbm_server_ctx {
   clbm_dtype dtype = CLBM_F16S;
+  bool sround = false;              // F16S: lattices round their stores stochastically
   double budget = 0;
   int max_active = 0;
   int check_interval = 100;
@@ -173,6 +174,7 @@ void worker_loop(clbm_server_ctx* s) {
       dom.stream = nullptr;
       dom.in_place = 0;   // the batched step works on two buffers
       int rc = clbm_create(&dom, p.req.K, p.req.n, p.req.U_lid, p.req.body_force, s->dtype, &a.h);
+      if (rc == CLBM_OK && s->sround) rc = clbm_set_rounding(a.h, CLBM_ROUND_STOCHASTIC);
       if (rc == CLBM_OK) rc = clbm_batch_add(s->batch, a.h, &a.slot);
       a.t_admit = now(s);
       s->queue.pop_front();
@@ -353,6 +355,20 @@ int clbm_server_release(clbm_server s, int64_t id) {
   if (!valid(s)) return sfail(s, CLBM_ERR_ARG, "invalid server");
   std::lock_guard<std::mutex> lk(s->mu);
   if (!s->done.erase(id)) return sfail(s, CLBM_ERR_ARG, "unknown or unfinished request");
+  return CLBM_OK;
+}
+
+int clbm_server_set_rounding(clbm_server s, clbm_rounding mode) {
+  if (!valid(s)) return sfail(s, CLBM_ERR_ARG, "invalid server");
+  if (mode != CLBM_ROUND_NEAREST && mode != CLBM_ROUND_STOCHASTIC)
+    return sfail(s, CLBM_ERR_ARG, "unknown rounding mode");
+  const bool sr = mode == CLBM_ROUND_STOCHASTIC;
+  if (s->dtype == CLBM_F16R && !sr)
+    return sfail(s, CLBM_ERR_UNSUPPORTED, "the F16R form always rounds stochastically");
+  if (s->dtype != CLBM_F16R && s->dtype != CLBM_F16S && sr)
+    return sfail(s, CLBM_ERR_UNSUPPORTED, "stochastic rounding is an F16S option");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->sround = sr && s->dtype == CLBM_F16S;
   return CLBM_OK;
 }
 

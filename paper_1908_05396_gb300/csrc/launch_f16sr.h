@@ -15,4 +15,8 @@ cudaError_t launch_step_f16sr(const void* src, void* dst, const Geom& g, const P
                               const CheckBufs& cb, bool check, dim3 block, int npt, int64_t step,
                               cudaStream_t st);
 
+// Mark a filled F16S batch descriptor (fill_desc_f16) as rounding its
+// stores stochastically (batch.cuh, LatDesc::sround).
+void desc_set_sround_f16(void* out, int on);
+
 }  // namespace clbm

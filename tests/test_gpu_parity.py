@@ -268,13 +268,15 @@ def test_stochastic_rounding_is_an_f16s_two_buffer_option(clbm):
         info = lat.autotune(3)
         assert info["npt"] in (1, 5)
         with clbm.Batch("f16s", capacity=2) as batch:
+            batch.add(lat)                      # the persistent kernel rounds stochastically too
+            with pytest.raises(clbm.CLBMError):
+                lat.set_rounding("nearest")     # not while batched
+            with pytest.raises(clbm.CLBMError):
+                batch.set_lattice_launch(32, 2, 5, 2)
+        with clbm.Batch("f16s", capacity=2) as batch:
+            batch.set_lattice_launch(32, 2, 5, 2)
             with pytest.raises(clbm.CLBMError):
                 batch.add(lat)
-        lat.set_rounding("nearest")
-        with clbm.Batch("f16s", capacity=2) as batch:
-            batch.add(lat)
-            with pytest.raises(clbm.CLBMError):
-                lat.set_rounding("stochastic")
 
 
 def test_autotune_restores_state_and_keeps_parity(clbm):

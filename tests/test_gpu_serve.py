@@ -35,12 +35,21 @@ def _submit(srv, p, tol):
     return srv.submit(**p.kwargs(), tol=tol, max_steps=6000, keep_fields=True)
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s", "f16r"])
+def _server(clbm, form, **kw):
+    """A server of storage form `form`; "f16s_sr": F16S lattices with
+    stochastically rounded stores."""
+    srv = clbm.Server("f16s" if form == "f16s_sr" else form, **kw)
+    if form == "f16s_sr":
+        srv.set_rounding("stochastic")
+    return srv
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s", "f16s_sr", "f16r"])
 def test_same_result_alone_and_in_the_mix(clbm, dtype):
     probs = _requests()
-    tol = {"f16s": 1e-4, "f16r": 1e-5}.get(dtype, 1e-6)
+    tol = {"f16s": 1e-4, "f16s_sr": 1e-4, "f16r": 1e-5}.get(dtype, 1e-6)
     mixed = {}
-    with clbm.Server(dtype, hbm_budget_bytes=4e9, max_active=3, check_interval=50) as srv:
+    with _server(clbm, dtype, hbm_budget_bytes=4e9, max_active=3, check_interval=50) as srv:
         ids = []
         for k, p in enumerate(probs):
             ids.append(_submit(srv, p, tol))
@@ -49,7 +58,7 @@ def test_same_result_alone_and_in_the_mix(clbm, dtype):
             res = srv.wait(rid, timeout=120)
             mixed[k] = (res, srv.fields(rid))
     for k, p in enumerate(probs):
-        with clbm.Server(dtype, hbm_budget_bytes=4e9, max_active=1, check_interval=50) as srv:
+        with _server(clbm, dtype, hbm_budget_bytes=4e9, max_active=1, check_interval=50) as srv:
             rid = _submit(srv, p, tol)
             res = srv.wait(rid, timeout=120)
             rho, u, gd = srv.fields(rid)
