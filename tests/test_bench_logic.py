@@ -43,3 +43,25 @@ def test_form_names():
     assert bench.form_spec("f16s_sr") == ("f16s", False, "stochastic")
     assert bench.form_spec("f32_inplace") == ("f32", True, None)
     assert bench.form_spec("f16r") == ("f16r", False, None)
+
+
+def test_serving_bench_headline_and_forms(monkeypatch):
+    import types
+    import numpy as np
+    import bench
+    fake = types.SimpleNamespace(SOLVE_STATUS={0: "converged", 1: "max_steps", 3: "diverged"})
+    trace = [types.SimpleNamespace(problem=None, arrival=0.1 * k) for k in range(3)]
+    u = np.ones((3, 2, 2, 2))
+
+    def serve(clbm, tr, dtype, tol, cap, plateau, check):
+        res = [{"t_submit": 0.1 * k, "t_done": 1.0 + k, "status": 0, "steps": 100} for k in range(3)]
+        return res, [u * (1 + 1e-4 * (dtype != "f64")) for _ in tr], {"lattice_updates": 1e6,
+                                                                       "busy_seconds": 1.0}
+
+    monkeypatch.setattr(bench, "_serve_trace", serve)
+    monkeypatch.setattr(bench, "_solve_alone", lambda *a: ("converged", 100, u))
+    out = bench._serving_bench(fake, trace, 1e-7, 100, 20, 10, "three requests")
+    assert out["form"].startswith("f16s_sr")
+    assert set(out["other_forms"]) == {"f16r", "f16s", "f32"}
+    assert out["velocity_l2_vs_f64"]["within_bar"] == "3/3 at L2 <= 0.002"
+    assert out["speedup_vs_sequential_f64"] > 0
