@@ -61,7 +61,7 @@ def test_serving_bench_headline_and_forms(monkeypatch):
     monkeypatch.setattr(bench, "_serve_trace", serve)
     monkeypatch.setattr(bench, "_solve_alone", lambda *a: ("converged", 100, u))
     out = bench._serving_bench(fake, trace, 1e-7, 100, 20, 10, "three requests")
-    assert out["form"].startswith("f16s_sr")
-    assert set(out["other_forms"]) == {"f16r", "f16s", "f32"}
+    assert out["form"] == "f16r"
+    assert set(out["other_forms"]) == {"f16s_sr", "f16s", "f32"}
     assert out["velocity_l2_vs_f64"]["within_bar"] == "3/3 at L2 <= 0.002"
     assert out["speedup_vs_sequential_f64"] > 0
