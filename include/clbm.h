@@ -62,7 +62,8 @@ extern "C" {
  *   CLBM_F16R : (f - w [rho0 + drho + 3 (rho0 + drho)(e . u)]) * 1024 in
  *               FP16 with stochastic rounding, relative to the writing node's
  *               own (drho, 3 (rho0 + drho) u), which is stored beside the
- *               populations as four FP16 values; collision in FP32.  Removing
+ *               populations as four FP16 values (scaled by 1024); collision
+ *               in FP32.  Removing
  *               the first-order equilibrium before rounding keeps steady
  *               states close to FP64.  16 more bytes per node update than
  *               F16S.  Not available to clbm_step_noalloc, to in-place
@@ -257,7 +258,8 @@ typedef struct clbm_batch_ctx* clbm_batch;
 int clbm_batch_create(clbm_dtype dtype, int capacity, int check_interval, void* stream,
                       clbm_batch* out);
 /* Attach h (same dtype and device, not in another batch, 19 x padded nodes
- * < 2^31; an in-place lattice only in the one-launch-per-lattice mode, else
+ * < 2^31; an in-place lattice only in the one-launch-per-lattice mode, an
+ * F16S lattice with stochastic rounding only in the persistent mode, else
  * CLBM_ERR_UNSUPPORTED); its queued work is waited for; *slot receives its
  * slot. */
 int clbm_batch_add(clbm_batch b, clbm_handle h, int* slot);
@@ -284,7 +286,8 @@ int clbm_batch_stats_all(clbm_batch b, double* residual, double* mass, int* dive
  * attached. */
 int clbm_batch_set_launch(clbm_batch b, int block_x, int block_y, int zc, int blocks_per_sm);
 /* One launch per lattice instead of the persistent kernel (FP64, FP32,
- * F16S; CLBM_ERR_UNSUPPORTED for F16R, whose rounding is seeded by the batch's
+ * F16S; CLBM_ERR_UNSUPPORTED for F16R and while an F16S lattice with
+ * stochastic rounding is attached, whose rounding is seeded by the batch's
  * device-side step count): every step launches each attached lattice's own
  * step kernel (block_x x block_y threads, a multiple of 32 and <= 256; npt 1,
  * or 5 for the register-capped kernel), the lattices spread over `streams`
@@ -295,7 +298,8 @@ int clbm_batch_set_launch(clbm_batch b, int block_x, int block_y, int zc, int bl
  * lattices.  clbm_batch_set_launch() returns to the persistent kernel. */
 int clbm_batch_set_lattice_launch(clbm_batch b, int block_x, int block_y, int npt, int streams);
 /* Time block shapes x zc x blocks-per-SM x register cap of the persistent
- * kernel and, except for F16R, block shapes x kernel variant x streams of one
+ * kernel and, except for F16R and stochastically rounding F16S lattices,
+ * block shapes x kernel variant x streams of one
  * launch per lattice, on the attached lattices (states saved and restored),
  * and keep the fastest (only the latter while an in-place lattice is
  * attached).  Persistent kernel: *blocks_per_sm is negative when

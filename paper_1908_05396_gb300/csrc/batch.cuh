@@ -289,7 +289,7 @@ void fill_desc_t(void* out, double lam, const Geom& g, const PhysParams& P, cons
   void fill_desc_##SUFFIX(void* out, const Geom& g, const PhysParams& P, const void* cur,        \
                           const void* other, const void* ref_cur, const void* ref_other,       \
                           void* uprev, int tx, int ty, int twl, int slot, unsigned so) {       \
-    /* the F16R form carries unscaled deviations; FP16-shifted ones are scaled */            \
+    /* FP16 storage (F16S, F16R) carries its deviations scaled by 1024 */                    \
     fill_desc_t<R>(out, double(1 << log2_scale<S>()), g, P, cur, other, ref_cur,             \
                    ref_other, uprev, tx, ty, twl, slot, so);                                   \
   }                                                                                            \
