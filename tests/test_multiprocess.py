@@ -33,7 +33,7 @@ def _rank_main(rank, ws, port, out):
 
 def test_max_over_ranks_and_whole_job_rate_gloo_two_ranks():
     ws, port = 2, _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:   # no fork of a threaded process
         out = m.dict()
         mp.spawn(_rank_main, args=(ws, port, out), nprocs=ws, join=True)
         res = dict(out)
